@@ -1,0 +1,235 @@
+/*
+ * zmc.h — C ABI of the GB300 parameter-grid direct Monte Carlo library.
+ *
+ * The method (arXiv:1910.01965, "ZMCintegral-v5"): for every point x of a
+ * Cartesian parameter grid built from M per-parameter value lists (Sec. 2),
+ * estimate f(x) = \int dy g(y; x) over an N-dimensional box (Eq. 1) by the
+ * direct (plain) Monte Carlo method (Sec. 1, Sec. 2), repeated over T
+ * independent trials (Sec. 3.2), and return one value per grid point as a
+ * multi-dimensional grid (Sec. 2).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a zmc_status.  Nothing throws across the ABI.  On any
+ *    error the outputs are left untouched and zmc_last_error() returns a
+ *    message for the calling thread.
+ *  - Grid order is C order over the lists: the flat index p has the last list
+ *    varying fastest, as numpy's indexing='ij'.  Output arrays hold one FP64
+ *    value per grid point in that order.
+ *  - Random numbers: sample s, dimension k of grid point p in trial t uses the
+ *    32-bit word w = s*N + k, lane (w mod 4) of Philox4x32-10 (Salmon et al.,
+ *    SC'11) with counter (floor(w/4), t, p mod 2^32, p >> 32) and key
+ *    (seed mod 2^32, seed >> 32); the word r becomes
+ *    u = (2*(r >> 9) + 1) * 2^-24 and y_k = a_k + (b_k - a_k) * u.  The
+ *    stream depends only on (seed, p, t, s, k), so any slice of the grid
+ *    reproduces the full-grid values bit for bit.
+ *  - Estimates: I_t = V * sum_s g / S with V = prod_k (b_k - a_k);
+ *    mean = sum_t I_t / T; err = sqrt(sum_t (I_t - mean)^2 / (T (T-1)))
+ *    (NaN when T = 1); errw = V * sqrt(mean_t[(s2_t - s1_t^2/S)/(S-1)]/(T S)),
+ *    the pooled within-trial standard error (NaN when S = 1).
+ *  - Host buffers belong to the caller; the library copies what it needs
+ *    before returning.  Device buffers (ZMC_MEM_DEVICE) belong to the caller
+ *    and must stay valid until the work enqueued on the stream completes.
+ *  - One CUDA device: the current device of the calling thread.
+ */
+#ifndef ZMC_H_
+#define ZMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZMC_ABI_VERSION 1
+#define ZMC_MAX_N 8   /* integration dimensions   */
+#define ZMC_MAX_M 16  /* parameters (value lists) */
+
+typedef enum {
+  ZMC_OK = 0,
+  ZMC_EINVAL = 1,      /* an argument is out of range            */
+  ZMC_ENOMEM = 2,      /* device or host memory could not be had */
+  ZMC_ECUDA = 3,       /* a CUDA call failed                     */
+  ZMC_ETIMEDOUT = 4,   /* a bounded wait ran out                 */
+  ZMC_ECANCELED = 5,   /* the request was cancelled              */
+  ZMC_EBUSY = 6,       /* the resource is in use                 */
+  ZMC_ENOTFOUND = 7    /* unknown integrand id or ticket         */
+} zmc_status;
+
+typedef enum {
+  ZMC_FP64 = 0,        /* FP64 samples, integrand and sums                 */
+  ZMC_FP32 = 1,        /* FP32 samples and integrand, plain FP32 lane sums  */
+  ZMC_FP32_KAHAN = 2   /* FP32 samples and integrand, Kahan FP32 lane sums  */
+} zmc_precision;       /* cross-lane reduction and the statistics: FP64    */
+
+/* Integrand registry (compiled in).  x has M entries, y has N entries. */
+enum {
+  ZMC_G_CONST = 0,    /* g = 1                                      any M  */
+  ZMC_G_COSPROD = 1,  /* g = prod_k cos(x_k y_k)                    M = N  */
+  ZMC_G_GAUSS03 = 2,  /* g = exp(-sum_k (y_k - x_k)^2 / (2 0.3^2))  M = N  */
+  ZMC_G_POLY = 3,     /* g = prod_k (1 + x_k y_k^2)                 M = N  */
+  ZMC_G_OSC01 = 4,    /* g = cos(sum_k x_k y_k + 0.1 sum_k y_k^2)   M = N  */
+  ZMC_G_SINSUM = 5,   /* g = sin(sum_k y_k + sum_l x_l)             any M  */
+                      /*     (the test integrand of Eq. 2 and Eq. 4)       */
+  ZMC_G_COUNT = 6
+};
+
+enum { ZMC_MEM_HOST = 0, ZMC_MEM_DEVICE = 1 };
+
+/* zmc_scan_desc.flags */
+enum {
+  ZMC_F_TIMINGS = 1,  /* record CUDA-event timings into zmc_scan_out; the
+                         call then waits for its work before returning   */
+  ZMC_F_SYNC = 2      /* wait for the enqueued work before returning      */
+};
+
+/*
+ * One scan request.  Initialise with zmc_scan_desc_init() and set fields.
+ *  integrand_id, N      registry id and dimension N in [1, ZMC_MAX_N]
+ *  lo, hi               HOST arrays of N finite doubles, hi[k] > lo[k]
+ *  M, list_len          M in [1, ZMC_MAX_M]; HOST array of M lengths >= 1;
+ *                       the grid has P = prod list_len points (P < 2^62)
+ *  list_vals            the M lists concatenated (sum list_len doubles);
+ *                       host or device memory according to `mem`
+ *  samples_per_point    S >= 1, with S * N < 2^34
+ *  trials               T in [1, 2^31)
+ *  seed                 64-bit Philox key
+ *  precision            a zmc_precision
+ *  mem                  ZMC_MEM_HOST: list_vals and outputs are host memory
+ *                       and the call is synchronous.  ZMC_MEM_DEVICE: they
+ *                       are device memory and the call only enqueues work
+ *                       on `stream` (unless flags ask to wait).
+ *  first_index, count   the slice [first_index, first_index + count) of the
+ *                       flat grid to evaluate; count = -1 means to the end.
+ *                       count = 0 is a valid no-op.  Outputs hold `count`
+ *                       entries, for the slice's points in order.
+ *  stream               cudaStream_t to launch on (NULL = the library's own
+ *                       non-blocking stream)
+ *  workspace            optional device scratch of workspace_bytes bytes
+ *                       (see zmc_workspace_size); NULL = the library takes
+ *                       it from its stream-ordered memory pool
+ *  tile_lanes, tile_splits, tile_block
+ *                       0 = chosen by the planner/autotuner; otherwise
+ *                       lanes per unit-split (power of two <= tile_block),
+ *                       sample splits per (point, trial) unit, and threads
+ *                       per block (64..1024, multiple of 32)
+ *  flags                ZMC_F_* bits
+ */
+typedef struct zmc_scan_desc {
+  int integrand_id;
+  int N;
+  const double* lo;
+  const double* hi;
+  int M;
+  const int64_t* list_len;
+  const double* list_vals;
+  int64_t samples_per_point;
+  int trials;
+  uint64_t seed;
+  int precision;
+  int mem;
+  int64_t first_index;
+  int64_t count;
+  void* stream;
+  void* workspace;
+  size_t workspace_bytes;
+  int tile_lanes;
+  int tile_splits;
+  int tile_block;
+  int flags;
+} zmc_scan_desc;
+
+/*
+ * Outputs of one scan.  mean and err are required (count entries each);
+ * errw, s1 and s2 are optional (NULL = not written).  s1 and s2 receive the
+ * per-trial sums sum_s g and sum_s g^2, count*T entries, trial fastest.
+ * All arrays are host or device memory according to desc->mem.
+ * The remaining fields are written by the call: the tile configuration it
+ * used and, with ZMC_F_TIMINGS, CUDA-event times in milliseconds.
+ */
+typedef struct zmc_scan_out {
+  double* mean;
+  double* err;
+  double* errw;
+  double* s1;
+  double* s2;
+  int tile_lanes;
+  int tile_splits;
+  int tile_block;
+  int launches;        /* kernels this call launched                      */
+  float h2d_ms;        /* host->device copies (ZMC_MEM_HOST only)          */
+  float kernel_ms;     /* the sampling kernel                              */
+  float finalize_ms;   /* the cross-split reduction and statistics kernel  */
+  float d2h_ms;        /* device->host copies (ZMC_MEM_HOST only)          */
+  float total_ms;      /* first event to last event                        */
+} zmc_scan_out;
+
+typedef struct zmc_integrand_info {
+  int id;
+  char name[32];
+  int m_rule;          /* 0: any M;  1: M must equal N                    */
+} zmc_integrand_info;
+
+typedef struct zmc_device_info {
+  int device;
+  int sm_count;
+  int cc_major;
+  int cc_minor;
+  int max_threads_per_sm;
+  int clock_khz;       /* reported maximum SM clock                       */
+  size_t total_mem;
+  char name[96];
+} zmc_device_info;
+
+/* ABI version (ZMC_ABI_VERSION of the built library). */
+int zmc_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  The string
+ * stays valid until the next call on the same thread. */
+const char* zmc_last_error(void);
+
+/* Fill a descriptor with defaults: FP32_KAHAN, host memory, the whole grid,
+ * library stream, planner-chosen tiles, T = 1, S = 1.  Returns ZMC_OK, or
+ * ZMC_EINVAL for a NULL pointer. */
+int zmc_scan_desc_init(zmc_scan_desc* d);
+
+/* Registry lookup; ZMC_ENOTFOUND for an unknown id. */
+int zmc_integrand_info_get(int id, zmc_integrand_info* info);
+
+/* Properties of the current device; ZMC_ECUDA when there is none. */
+int zmc_device_info_get(zmc_device_info* info);
+
+/*
+ * Check a descriptor without touching a GPU: ZMC_OK if zmc_scan_ex would
+ * accept it, else ZMC_EINVAL / ZMC_ENOTFOUND with zmc_last_error() set.
+ * For ZMC_MEM_HOST the pointers are dereferenced only for lo, hi and list_len.
+ */
+int zmc_validate(const zmc_scan_desc* d);
+
+/*
+ * Device scratch that zmc_scan_ex needs for `d` with its tile configuration
+ * (after planning): 16 bytes per (point, trial, split) for the FP64 partial
+ * sums, plus the device copy of the lists and of the outputs when
+ * d->mem == ZMC_MEM_HOST.  Touches no GPU when the tiles are given
+ * explicitly; otherwise it may query the device for its SM count.
+ */
+int zmc_workspace_size(const zmc_scan_desc* d, size_t* bytes);
+
+/*
+ * The simple entry point (Sec. 2: a grid of parameters in, a grid of
+ * integrals out).  All pointers are HOST memory; precision FP32_KAHAN;
+ * the whole grid; synchronous.  out_mean and out_err hold P doubles.
+ */
+int zmc_scan(int integrand_id, int N, const double* lo, const double* hi,
+             int M, const int64_t* list_len, const double* list_vals,
+             int64_t samples_per_point, int trials, uint64_t seed,
+             double* out_mean, double* out_err);
+
+/* The general entry point: every option of zmc_scan_desc. */
+int zmc_scan_ex(const zmc_scan_desc* d, zmc_scan_out* o);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZMC_H_ */
