@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the parameter-grid direct Monte Carlo scan on GB300.
+
+One step = one full scan of the workload (every grid point, every trial,
+every sample: the sampling kernel and the finalize kernel) with inputs and
+outputs resident in device memory.  Default workload: the Gaussian integrand
+on [-1,1]^4 over a 100 x 100 x 100 x 1 parameter grid, 2^14 samples x 4
+trials per point, FP32 evaluation with Kahan-compensated lane sums.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MC evals/s on 1 GB300 and % FP32/SFU peak vs FP64 path; "
+          "p50/p99 scan latency")
+
+# Algorithmic operations per integrand evaluation, from the method's steps
+# (counted per sample of N dimensions; see the measurement section of the
+# design notes): Philox4x32-10 = 10 rounds x (2 wide multiplies + 2 three-input
+# XORs) per 4 words -> 10 N; word -> u and u -> y: 2 N; the integrand; the
+# lane accumulation of g and g^2.
+INTEGRAND_OPS = {
+    0: lambda N: 0,              # const (draws no samples)
+    1: lambda N: 3 * N - 1,      # cos-product: x*y, cos, product
+    2: lambda N: 2 * N + 2,      # Gaussian: (y-x), square-accumulate; scale, exp
+    3: lambda N: 3 * N - 1,      # polynomial: y^2, 1 + x y^2, product
+    4: lambda N: 2 * N + 2,      # oscillatory: x*y and y^2 accumulations; combine, cos
+    5: lambda N: N + 2,          # sine-sum: y accumulation; + sum x, sin
+}
+ACCUM_OPS = {0: 2, 1: 2, 2: 9}   # FP64, FP32: add + fma; Kahan: g^2 + 2 x 4
+
+
+def ops_per_eval(gid: int, N: int, prec: int) -> int:
+    rng = 0 if gid == 0 else 10 * N + 2 * N
+    return rng + INTEGRAND_OPS[gid](N) + ACCUM_OPS[prec]
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ distributed --
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------- workloads --
+def bench_workload(name: str):
+    from paper_1910_01965_gb300 import workloads as wl
+    if name == "gauss_1e5":   # the same scan on a 10 x 100 x 100 x 1 grid (profiling)
+        spec = wl.scan_gauss_1e6()
+        spec.lists[0] = spec.lists[0][:10]
+        spec.name = "gauss03_N4_P1e5_S2^14_T4"
+        return spec
+    return {"gauss_1e6": wl.scan_gauss_1e6, "osc_1e4": wl.scan_osc_1e4,
+            "cosprod_100": wl.scan_cosprod_100}[name]()
+
+
+def traffic_per_launch(spec, n_unit_splits: int):
+    """DRAM bytes of one sampling-kernel launch from the committed ncu summary,
+    scaled by unit-splits; None when the kernel sources changed since."""
+    from paper_1910_01965_gb300 import build as B
+    path = os.path.join(ROOT, "profiles", "scan_kernel_gauss03_N4_fp32k.md")
+    if not os.path.exists(path):
+        return None
+    stamp = B.source_stamp()
+    per_us, src = None, None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_unit_split:"):
+            per_us = float(line.split(":", 1)[1].split()[0])
+        if line.startswith("kernel_source_stamp:"):
+            src = line.split(":", 1)[1].strip()
+    if per_us is None or src != stamp:
+        return None
+    return per_us * n_unit_splits
+
+
+# ------------------------------------------------------------- CPU oracle --
+def cpu_oracle_run(spec, seconds: float, seed: int = 4242):
+    """Time the oracle (as it stands) on a seeded sample of grid points sized
+    for about `seconds` of CPU work.  Returns (evals/s, cores, description)."""
+    from oracle import oracle
+    from paper_1910_01965_gb300 import workloads as wl
+    O = oracle.default()
+    cores = O.max_threads()
+    per_point = spec.trials * spec.samples
+    calib = wl.sample_points(spec.P, max(cores, 4), seed=seed + 1)
+    t0 = time.perf_counter()
+    O.scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
+                  spec.samples, spec.trials, spec.seed, calib)
+    rate = calib.size * per_point / max(time.perf_counter() - t0, 1e-6)
+    npts = int(max(cores, min(spec.P, seconds * rate / per_point)))
+    pts = wl.sample_points(spec.P, npts, seed=seed)
+    t0 = time.perf_counter()
+    O.scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
+                  spec.samples, spec.trials, spec.seed, pts)
+    dt = time.perf_counter() - t0
+    value = pts.size * per_point / dt
+    desc = ("%d of %d grid points (seeded sample), all %d trials x %d samples each: "
+            "%.3g evals in %.1f s" % (pts.size, spec.P, spec.trials, spec.samples,
+                                      pts.size * per_point, dt))
+    return value, cores, desc, pts.size * per_point, dt
+
+
+def run_reference(args, spec, world, rank):
+    if rank != 0:
+        return 0
+    from paper_1910_01965_gb300 import workloads as wl
+    from oracle import oracle
+    O = oracle.default()
+    cores = O.max_threads()
+    per_point = spec.trials * spec.samples
+    # size each step for ~args.ref_step_seconds of CPU work
+    calib = wl.sample_points(spec.P, max(cores, 4), seed=99)
+    t0 = time.perf_counter()
+    O.scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
+                  spec.samples, spec.trials, spec.seed, calib)
+    rate = calib.size * per_point / max(time.perf_counter() - t0, 1e-6)
+    npts = int(max(cores, min(spec.P, args.ref_step_seconds * rate / per_point)))
+    for w in range(args.warmup):
+        pts = wl.sample_points(spec.P, npts, seed=1000 + w)
+        O.scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                      spec.values, spec.samples, spec.trials, spec.seed, pts)
+    total = 0.0
+    for k in range(args.steps):
+        pts = wl.sample_points(spec.P, npts, seed=2000 + k)
+        t0 = time.perf_counter()
+        O.scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                      spec.values, spec.samples, spec.trials, spec.seed, pts)
+        total += time.perf_counter() - t0
+    evals = npts * per_point * args.steps
+    value = evals / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(spec.describe(), precision="fp64 (CPU oracle)"),
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step: %d seeded grid points of %d, all trials and "
+                                   "samples" % (npts, spec.P)},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- main --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="zmc", choices=["zmc", "reference"])
+    ap.add_argument("--workload", default="gauss_1e6")
+    ap.add_argument("--precision", default="fp32_kahan", choices=["fp32_kahan", "fp32", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=6.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world, rank, local = dist_setup()
+    spec = bench_workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, spec, world, rank)
+
+    import torch
+    from paper_1910_01965_gb300 import zmc
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        spec.seed = spec.seed + rank  # an independent problem per rank
+    zmc.load()
+    info = zmc.zmc_device_info_get()
+    prec = zmc.PRECISIONS[args.precision]
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    vals = torch.tensor(spec.values, dtype=torch.float64, device=dev)
+    mean = torch.empty(spec.P, dtype=torch.float64, device=dev)
+    err = torch.empty_like(mean)
+    errw = torch.empty_like(mean)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(p=prec, flags=zmc.ZMC_F_TIMINGS):
+        return zmc.scan_device(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                               vals, spec.samples, spec.trials, spec.seed, mean, err, errw,
+                               precision=p, stream=stream.cuda_stream, flags=flags)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms, launches = [], 0
+    for k in range(args.steps):
+        flush.zero_()                      # L2 flush, outside the timed events
+        ev[k][0].record(stream)
+        o = step()
+        ev[k][1].record(stream)
+        kernel_ms.append(o.kernel_ms)      # the sampling kernel, library events
+        launches += o.launches
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(world, sum(step_ms))
+    value = world * spec.evals * args.steps / (total_ms * 1e-3)
+
+    # roofline of the sampling kernel (the dominant one)
+    n_us = spec.P * spec.trials * o.tile_splits
+    ops = ops_per_eval(spec.integrand_id, spec.N, prec) * spec.evals
+    k_ms = statistics.mean(kernel_ms)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    f_max = None
+    if os.path.exists(peaks_path):
+        f_max = json.load(open(peaks_path)).get("sm_max_mhz")
+    f_src = "sm_max_mhz of MEASURED_PEAKS.json"
+    if not f_max:
+        f_max, f_src = info.clock_khz / 1e3, "device-reported maximum SM clock"
+    peak = info.sm_count * 128 * f_max * 1e6 / 1e12   # lane-ops per second, T
+    achieved = ops / (k_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": traffic_per_launch(spec, n_us),
+                "kernel": "scan_kernel (sampling)", "kernel_ms": k_ms,
+                "ops_per_eval": ops_per_eval(spec.integrand_id, spec.N, prec),
+                "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s)" % (
+                    info.sm_count, f_max, f_src)}
+
+    # end to end through the C ABI with host buffers (pinned)
+    h_vals = torch.tensor(spec.values, dtype=torch.float64).pin_memory().numpy()
+    h_mean = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+    h_err = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+    d_host, keep = zmc.make_desc(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                                 h_vals, spec.samples, spec.trials, spec.seed, prec)
+    o_host = zmc.zmc_scan_out()
+    o_host.mean = h_mean.ctypes.data_as(zmc._dp)
+    o_host.err = h_err.ctypes.data_as(zmc._dp)
+    zmc.zmc_scan_ex(d_host, o_host)        # warm
+    e2e_steps = max(3, min(args.steps, 5))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        zmc.zmc_scan_ex(d_host, o_host)
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": world * spec.evals * e2e_steps / e2e_s, "unit": "evals/s",
+           "h2d_bytes_per_step": int(h_vals.nbytes),
+           "d2h_bytes_per_step": int(h_mean.nbytes + h_err.nbytes),
+           "steps": e2e_steps, "api": "zmc_scan_ex (ZMC_MEM_HOST, pinned host buffers)"}
+
+    extra = {}
+    if rank == 0 and not args.no_fp64 and prec != zmc.ZMC_FP64:
+        step(zmc.ZMC_FP64, zmc.ZMC_F_SYNC)  # warm the FP64 kernel
+        o64 = step(zmc.ZMC_FP64)
+        fp64_v = spec.evals / (o64.total_ms * 1e-3)
+        extra["fp64_path"] = {"value": fp64_v, "unit": "evals/s", "ms_per_step": o64.total_ms,
+                              "kernel_ms": o64.kernel_ms,
+                              "fp32_over_fp64": value / world / fp64_v}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, cores, desc, ev_n, dt = cpu_oracle_run(spec, args.cpu_seconds)
+        cpu = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == zmc.ZMC_FP64 else "f32",
+            "data": "synthetic",
+            "config": dict(spec.describe(), precision=args.precision,
+                           parallelism="independent scan per GPU" if world > 1 else "1 GPU",
+                           tiles=[o.tile_lanes, o.tile_splits, o.tile_block],
+                           l2="256 MiB buffer written between timed steps"),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -91,7 +91,7 @@ enum {
  *                       the grid has P = prod list_len points (P < 2^62)
  *  list_vals            the M lists concatenated (sum list_len doubles);
  *                       host or device memory according to `mem`
- *  samples_per_point    S >= 1, with S * N < 2^34
+ *  samples_per_point    S >= 1, with S * N <= 2^34 - 2^20
  *  trials               T in [1, 2^31)
  *  seed                 64-bit Philox key
  *  precision            a zmc_precision
@@ -103,8 +103,8 @@ enum {
  *                       flat grid to evaluate; count = -1 means to the end.
  *                       count = 0 is a valid no-op.  Outputs hold `count`
  *                       entries, for the slice's points in order.
- *  stream               cudaStream_t to launch on (NULL = the library's own
- *                       non-blocking stream)
+ *  stream               cudaStream_t to launch on; NULL is the CUDA default
+ *                       (legacy) stream, as for other CUDA libraries
  *  workspace            optional device scratch of workspace_bytes bytes
  *                       (see zmc_workspace_size); NULL = the library takes
  *                       it from its stream-ordered memory pool
@@ -112,7 +112,7 @@ enum {
  *                       0 = chosen by the planner/autotuner; otherwise
  *                       lanes per unit-split (power of two <= tile_block),
  *                       sample splits per (point, trial) unit, and threads
- *                       per block (64..1024, multiple of 32)
+ *                       per block (64..512, multiple of 32)
  *  flags                ZMC_F_* bits
  */
 typedef struct zmc_scan_desc {
@@ -227,6 +227,16 @@ int zmc_scan(int integrand_id, int N, const double* lo, const double* hi,
 
 /* The general entry point: every option of zmc_scan_desc. */
 int zmc_scan_ex(const zmc_scan_desc* d, zmc_scan_out* o);
+
+/*
+ * Raw random words of one unit's stream: out[i] = word (first_word + i) of
+ * grid point p, trial t, under `seed` (the layout at the top of this file).
+ * Sample s, dimension k is word s*N + k.  out is HOST memory of nwords
+ * entries; first_word + nwords <= 2^34, nwords <= 2^30.  Computed on the GPU
+ * by the same Philox code the sampling kernels use.  Synchronous.
+ */
+int zmc_stream_words(uint64_t seed, int64_t p, int t, uint64_t first_word,
+                     int64_t nwords, uint32_t* out);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,317 @@
+// zmc_integrands.cuh — the compiled-in integrand registry, as device functors.
+//
+// Each functor evaluates g(y; x) (Eq. 1, Sec. 2) at one sample, reading the
+// sample's N raw Philox words.  The map of a word r to the box coordinate is
+// u = (2 (r >> 9) + 1) 2^-24, y = a + (b - a) u.
+//
+// Two families:
+//  * FP64 functors (suffix 64) form y exactly as written above in FP64 and
+//    evaluate g in FP64.
+//  * FP32 functors (suffix 32) build the float f = 1 + (r >> 9) 2^-23 from the
+//    word's bits, so u = f - (1 - 2^-24) and y = (b - a) f + A with
+//    A = a - (b - a)(1 - 2^-24).  Everything affine in y that depends only on
+//    (x, box) is folded, in FP64, into per-unit constants before the sample
+//    loop; each sample then costs one FFMA per dimension before the
+//    integrand's own arithmetic.  cos/sin use the SFU (MUFU) approximations,
+//    exp uses ex2.approx.
+//
+// `set(i, x_i, a_i, b_i)` receives parameter i and box side i (kPerDim: the
+// integrand pairs x_k with y_k, M == N); `add(x_i)` receives parameters of the
+// any-M integrands; `finish(lo, hi)` runs once after the parameters.  FP32
+// functors with kTable take their constants from per-block tables instead
+// (value / dim / load, below).
+#pragma once
+
+#include <cstdint>
+
+namespace zmc {
+
+constexpr double kOneMinusHalfUlp = 1.0 - 0x1p-24;     // 1 - 2^-24
+constexpr double kGaussSigma = 0.3;
+constexpr double kOscQuad = 0.1;
+// sqrt(log2(e) / (2 sigma^2)) for sigma = 0.3: scales (y - x) so that
+// exp(-(y-x)^2 / (2 sigma^2)) = 2^-(d^2).
+constexpr double kGaussScale = 2.83107266762673;  // to double precision
+
+__device__ __forceinline__ float unit_f12(uint32_t r) {
+  // 1 + (r>>9) 2^-23: one funnel shift of (0x7f : r) right by 9 places the
+  // exponent bits 0x7f << 23 = 0x3f800000 above the 23 high bits of r.
+  return __uint_as_float(__funnelshift_r(r, 0x7fu, 9));
+}
+
+__device__ __forceinline__ double unit_u64(uint32_t r) {
+  // 1 + (r>>9) 2^-23 built from bits, minus (1 - 2^-24): exactly
+  // (2 (r>>9) + 1) 2^-24.
+  const double d = __longlong_as_double(
+      static_cast<long long>(0x3FF0000000000000ull |
+                             (static_cast<uint64_t>(r >> 9) << 29)));
+  return d - kOneMinusHalfUlp;
+}
+
+__device__ __forceinline__ float ex2_approx(float v) {
+  float out;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(out) : "f"(v));
+  return out;
+}
+
+// ------------------------------------------------------------------ FP64 --
+template <int N>
+struct Const64 {
+  static constexpr bool kPerDim = false;
+  static constexpr bool kTable = false;
+  static constexpr bool kUsesSamples = false;
+  __device__ void add(double) {}
+  __device__ void finish(const double*, const double*) {}
+  __device__ double eval(const uint32_t*) const { return 1.0; }
+};
+
+template <int N>
+struct CosProd64 {
+  static constexpr bool kPerDim = true;
+  static constexpr bool kTable = false;
+  static constexpr bool kUsesSamples = true;
+  double x[N], w[N], a[N];
+  __device__ void set(int i, double xi, double ai, double bi) {
+    x[i] = xi; a[i] = ai; w[i] = bi - ai;
+  }
+  __device__ double eval(const uint32_t* r) const {
+    double g = cos(x[0] * fma(w[0], unit_u64(r[0]), a[0]));
+#pragma unroll
+    for (int k = 1; k < N; ++k) g *= cos(x[k] * fma(w[k], unit_u64(r[k]), a[k]));
+    return g;
+  }
+};
+
+template <int N>
+struct Gauss64 {
+  static constexpr bool kPerDim = true;
+  static constexpr bool kTable = false;
+  static constexpr bool kUsesSamples = true;
+  double x[N], w[N], a[N];
+  __device__ void set(int i, double xi, double ai, double bi) {
+    x[i] = xi; a[i] = ai; w[i] = bi - ai;
+  }
+  __device__ double eval(const uint32_t* r) const {
+    double q = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const double d = fma(w[k], unit_u64(r[k]), a[k]) - x[k];
+      q += d * d;
+    }
+    return exp(-q / (2.0 * kGaussSigma * kGaussSigma));
+  }
+};
+
+template <int N>
+struct Poly64 {
+  static constexpr bool kPerDim = true;
+  static constexpr bool kTable = false;
+  static constexpr bool kUsesSamples = true;
+  double x[N], w[N], a[N];
+  __device__ void set(int i, double xi, double ai, double bi) {
+    x[i] = xi; a[i] = ai; w[i] = bi - ai;
+  }
+  __device__ double eval(const uint32_t* r) const {
+    double g = 1.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const double y = fma(w[k], unit_u64(r[k]), a[k]);
+      g *= 1.0 + x[k] * y * y;
+    }
+    return g;
+  }
+};
+
+template <int N>
+struct Osc64 {
+  static constexpr bool kPerDim = true;
+  static constexpr bool kTable = false;
+  static constexpr bool kUsesSamples = true;
+  double x[N], w[N], a[N];
+  __device__ void set(int i, double xi, double ai, double bi) {
+    x[i] = xi; a[i] = ai; w[i] = bi - ai;
+  }
+  __device__ double eval(const uint32_t* r) const {
+    double lin = 0.0, quad = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const double y = fma(w[k], unit_u64(r[k]), a[k]);
+      lin += x[k] * y;
+      quad += y * y;
+    }
+    return cos(lin + kOscQuad * quad);
+  }
+};
+
+template <int N>
+struct SinSum64 {
+  static constexpr bool kPerDim = false;
+  static constexpr bool kTable = false;
+  static constexpr bool kUsesSamples = true;
+  double xsum, w[N], a[N];
+  __device__ void add(double xi) { xsum += xi; }
+  __device__ void finish(const double* lo, const double* hi) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) { a[k] = lo[k]; w[k] = hi[k] - lo[k]; }
+  }
+  __device__ double eval(const uint32_t* r) const {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) s += fma(w[k], unit_u64(r[k]), a[k]);
+    return sin(s + xsum);
+  }
+};
+
+// ------------------------------------------------------------------ FP32 --
+// FP32 functors with a per-value table (kTable): while the lists are staged
+// into shared memory each value x of list k becomes a float2 of per-value
+// constants (value(k, x, a, b)), and each dimension gets up to three FP32
+// per-dimension constants (dim(k, a, b, out)), both computed once per block in
+// FP64.  A thread then sets up a unit with table lookups only (load()).
+
+template <int N>
+struct Const32 {
+  static constexpr bool kPerDim = false;
+  static constexpr bool kTable = false;
+  static constexpr bool kUsesSamples = false;
+  __device__ void add(double) {}
+  __device__ void finish(const double*, const double*) {}
+  __device__ float eval(const uint32_t*) const { return 1.0f; }
+};
+
+// cos(x y) = cos(B f + C), B = x (b - a), C = x A.
+template <int N>
+struct CosProd32 {
+  static constexpr bool kPerDim = true;
+  static constexpr bool kTable = true;
+  static constexpr bool kUsesSamples = true;
+  float B[N], C[N];
+  static __device__ float2 value(int, double x, double a, double b) {
+    const double w = b - a;
+    return make_float2(static_cast<float>(x * w),
+                       static_cast<float>(x * (a - w * kOneMinusHalfUlp)));
+  }
+  static __device__ void dim(int, double, double, float*) {}
+  __device__ void load(int k, float2 v, const float*) { B[k] = v.x; C[k] = v.y; }
+  __device__ float eval(const uint32_t* r) const {
+    float g = __cosf(fmaf(B[0], unit_f12(r[0]), C[0]));
+#pragma unroll
+    for (int k = 1; k < N; ++k) g *= __cosf(fmaf(B[k], unit_f12(r[k]), C[k]));
+    return g;
+  }
+};
+
+// exp(-(y-x)^2/(2 s^2)) per dimension = 2^-(d^2), d = c (y - x) = B f + C,
+// B = c (b - a) per dimension, C = c (A - x) per value.
+template <int N>
+struct Gauss32 {
+  static constexpr bool kPerDim = true;
+  static constexpr bool kTable = true;
+  static constexpr bool kUsesSamples = true;
+  float B[N], C[N];
+  static __device__ float2 value(int, double x, double a, double b) {
+    const double w = b - a;
+    return make_float2(static_cast<float>((a - w * kOneMinusHalfUlp - x) * kGaussScale), 0.f);
+  }
+  static __device__ void dim(int, double a, double b, float* out) {
+    out[0] = static_cast<float>((b - a) * kGaussScale);
+  }
+  __device__ void load(int k, float2 v, const float* d) { B[k] = d[0]; C[k] = v.x; }
+  __device__ float eval(const uint32_t* r) const {
+    float d = fmaf(B[0], unit_f12(r[0]), C[0]);
+    float q = d * d;
+#pragma unroll
+    for (int k = 1; k < N; ++k) {
+      d = fmaf(B[k], unit_f12(r[k]), C[k]);
+      q = fmaf(d, d, q);
+    }
+    return ex2_approx(-q);
+  }
+};
+
+// prod (1 + x y^2), y = W f + A (per dimension), X = x (per value).
+template <int N>
+struct Poly32 {
+  static constexpr bool kPerDim = true;
+  static constexpr bool kTable = true;
+  static constexpr bool kUsesSamples = true;
+  float W[N], A[N], X[N];
+  static __device__ float2 value(int, double x, double, double) {
+    return make_float2(static_cast<float>(x), 0.f);
+  }
+  static __device__ void dim(int, double a, double b, float* out) {
+    const double w = b - a;
+    out[0] = static_cast<float>(w);
+    out[1] = static_cast<float>(a - w * kOneMinusHalfUlp);
+  }
+  __device__ void load(int k, float2 v, const float* d) { W[k] = d[0]; A[k] = d[1]; X[k] = v.x; }
+  __device__ float eval(const uint32_t* r) const {
+    float y = fmaf(W[0], unit_f12(r[0]), A[0]);
+    float g = fmaf(X[0] * y, y, 1.0f);
+#pragma unroll
+    for (int k = 1; k < N; ++k) {
+      y = fmaf(W[k], unit_f12(r[k]), A[k]);
+      g *= fmaf(X[k] * y, y, 1.0f);
+    }
+    return g;
+  }
+};
+
+// cos(sum_k y_k (x_k + 0.1 y_k)), y = W f + A (per dimension), X = x.
+template <int N>
+struct Osc32 {
+  static constexpr bool kPerDim = true;
+  static constexpr bool kTable = true;
+  static constexpr bool kUsesSamples = true;
+  float W[N], A[N], X[N];
+  static __device__ float2 value(int, double x, double, double) {
+    return make_float2(static_cast<float>(x), 0.f);
+  }
+  static __device__ void dim(int, double a, double b, float* out) {
+    const double w = b - a;
+    out[0] = static_cast<float>(w);
+    out[1] = static_cast<float>(a - w * kOneMinusHalfUlp);
+  }
+  __device__ void load(int k, float2 v, const float* d) { W[k] = d[0]; A[k] = d[1]; X[k] = v.x; }
+  __device__ float eval(const uint32_t* r) const {
+    float y = fmaf(W[0], unit_f12(r[0]), A[0]);
+    float ph = y * fmaf(static_cast<float>(kOscQuad), y, X[0]);
+#pragma unroll
+    for (int k = 1; k < N; ++k) {
+      y = fmaf(W[k], unit_f12(r[k]), A[k]);
+      ph = fmaf(y, fmaf(static_cast<float>(kOscQuad), y, X[k]), ph);
+    }
+    return __cosf(ph);
+  }
+};
+
+// sin(sum_k W_k f_k + C0), C0 = (sum_k A_k + sum_l x_l) reduced mod 2 pi in FP64.
+template <int N>
+struct SinSum32 {
+  static constexpr bool kPerDim = false;
+  static constexpr bool kTable = false;
+  static constexpr bool kUsesSamples = true;
+  double xsum;
+  float W[N], C0;
+  __device__ void add(double xi) { xsum += xi; }
+  __device__ void finish(const double* lo, const double* hi) {
+    double c = xsum;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const double w = hi[k] - lo[k];
+      W[k] = static_cast<float>(w);
+      c += lo[k] - w * kOneMinusHalfUlp;
+    }
+    const double two_pi = 6.283185307179586476925;
+    c = c - two_pi * floor(c / two_pi);
+    C0 = static_cast<float>(c);
+  }
+  __device__ float eval(const uint32_t* r) const {
+    float s = C0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) s = fmaf(W[k], unit_f12(r[k]), s);
+    return __sinf(s);
+  }
+};
+
+}  // namespace zmc

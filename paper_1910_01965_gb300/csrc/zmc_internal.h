@@ -1,0 +1,78 @@
+// zmc_internal.h — types shared by the runtime and the kernel translation units.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/zmc.h"
+
+namespace zmc {
+
+// Philox4x32-10 constants (Salmon et al., SC'11).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Largest list staging in shared memory (doubles).
+constexpr int kMaxSmemVals = 4096;
+
+// Everything one launch of the sampling kernel needs, passed by value.
+// A "unit" is one (grid point, trial) pair; its S samples are cut into
+// `splits` contiguous ranges of sample groups, and each range (a
+// "unit-split") is summed by `lanes` threads of one block.
+struct ScanArgs {
+  int64_t first;        // first flat grid index of the slice
+  int64_t count;        // grid points in the slice
+  int64_t S;            // samples per unit
+  int64_t ngroups;      // sample groups per unit: ceil(S / G)
+  int64_t gps;          // sample groups per split: ceil(ngroups / splits)
+  int64_t n_us;         // unit-splits: count * T * splits
+  int32_t T;
+  int32_t M;
+  int32_t splits;
+  int32_t lanes;        // power of two, <= blockDim.x
+  int32_t lanes_log2;
+  int32_t nvals;        // total list length
+  int32_t stage_smem;   // 1: lists copied to shared memory first
+  int32_t idx32;        // 1: every flat index of the slice is below 2^32
+  const double* vals;   // device, the M lists concatenated
+  int64_t len[ZMC_MAX_M];
+  int32_t off[ZMC_MAX_M];
+  double lo[ZMC_MAX_N];
+  double hi[ZMC_MAX_N];
+  uint32_t rk0[10];     // Philox round keys: key0 + r * W0
+  uint32_t rk1[10];     // Philox round keys: key1 + r * W1
+  double* partial;      // device, [n_us][2] FP64 (sum g, sum g^2)
+};
+
+struct FinalizeArgs {
+  int64_t count;
+  int64_t S;
+  int32_t T;
+  int32_t splits;
+  double V;
+  const double* partial;
+  double* mean;
+  double* err;
+  double* errw;   // may be null
+  double* s1;     // may be null, [count][T]
+  double* s2;     // may be null, [count][T]
+};
+
+// Samples per group G and Philox calls per group C for dimension N:
+// G samples use exactly G*N = 4*C consecutive words.
+constexpr int group_samples(int N) { return (N % 4 == 0) ? 1 : (N % 2 == 0 ? 2 : 4); }
+constexpr int group_calls(int N) { return N * group_samples(N) / 4; }
+
+// Launches of one precision's sampling kernel for (integrand, N).
+// Returns a CUDA error code (0 = success).
+typedef int (*ScanLaunchFn)(const ScanArgs& a, int block, int64_t grid,
+                            size_t smem, void* stream);
+
+ScanLaunchFn scan_launcher(int precision, int integrand, int N);
+int finalize_launch(const FinalizeArgs& a, void* stream);
+
+int stream_words_launch(uint64_t seed, int64_t p, int t, uint64_t first_word,
+                        int64_t nwords, uint32_t* out_dev, void* stream);
+
+}  // namespace zmc

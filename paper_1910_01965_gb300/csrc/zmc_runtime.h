@@ -1,0 +1,43 @@
+// zmc_runtime.h — host-side helpers shared by the runtime translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "zmc_internal.h"
+
+namespace zmc {
+
+struct TilePlan {
+  int lanes = 32;   // threads summing one unit-split (power of two)
+  int splits = 1;   // sample ranges per (point, trial) unit
+  int block = 256;  // threads per block
+};
+
+// Byte offsets of each region inside one scan's device scratch.
+struct ScanLayout {
+  size_t partial, partial_bytes;
+  size_t vals, mean, err, errw, s1, s2;  // SIZE_MAX when not used
+  size_t total;
+};
+
+int fail(int status, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+const char* last_error();
+
+int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out);
+TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count, int threads_per_sm,
+                    int lanes_req, int splits_req, int block_req);
+int plan_for(const zmc_scan_desc* d, int64_t count, TilePlan* tp);
+ScanLayout layout_for(const zmc_scan_desc* d, int64_t count, const TilePlan& tp);
+double box_volume(const zmc_scan_desc* d);
+void fill_scan_args(const zmc_scan_desc* d, int64_t count, const TilePlan& tp,
+                    const double* vals_dev, double* partial_dev, ScanArgs* a);
+int launch_scan_args(const zmc_scan_desc* d, const ScanArgs& a, const TilePlan& tp,
+                     cudaStream_t stream);
+int scan_ex(const zmc_scan_desc* d, zmc_scan_out* o);
+
+}  // namespace zmc

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of the C ABI in include/zmc.h (libzmc.so).
+
+Argument marshalling only: every step of a scan runs in the library's CUDA
+kernels.  The names mirror the C entry points (``zmc_scan``, ``zmc_scan_ex``,
+...).  ``scan()`` and ``scan_device()`` are conveniences that fill a
+``zmc_scan_desc`` from numpy arrays or torch CUDA tensors and call
+``zmc_scan_ex``.  Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIBRARY = os.path.join(_PKG, "libzmc.so")
+
+ZMC_OK, ZMC_EINVAL, ZMC_ENOMEM, ZMC_ECUDA, ZMC_ETIMEDOUT, ZMC_ECANCELED, \
+    ZMC_EBUSY, ZMC_ENOTFOUND = range(8)
+ZMC_FP64, ZMC_FP32, ZMC_FP32_KAHAN = range(3)
+ZMC_G_CONST, ZMC_G_COSPROD, ZMC_G_GAUSS03, ZMC_G_POLY, ZMC_G_OSC01, \
+    ZMC_G_SINSUM, ZMC_G_COUNT = range(7)
+ZMC_MEM_HOST, ZMC_MEM_DEVICE = 0, 1
+ZMC_F_TIMINGS, ZMC_F_SYNC = 1, 2
+ZMC_MAX_N, ZMC_MAX_M = 8, 16
+
+STATUS_NAMES = {0: "ZMC_OK", 1: "ZMC_EINVAL", 2: "ZMC_ENOMEM", 3: "ZMC_ECUDA",
+                4: "ZMC_ETIMEDOUT", 5: "ZMC_ECANCELED", 6: "ZMC_EBUSY",
+                7: "ZMC_ENOTFOUND"}
+PRECISIONS = {"fp64": ZMC_FP64, "fp32": ZMC_FP32, "fp32_kahan": ZMC_FP32_KAHAN}
+
+
+class ZmcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class zmc_scan_desc(ctypes.Structure):
+    _fields_ = [("integrand_id", ctypes.c_int), ("N", ctypes.c_int),
+                ("lo", _dp), ("hi", _dp), ("M", ctypes.c_int),
+                ("list_len", _i64p), ("list_vals", _dp),
+                ("samples_per_point", ctypes.c_int64), ("trials", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
+                ("mem", ctypes.c_int), ("first_index", ctypes.c_int64),
+                ("count", ctypes.c_int64), ("stream", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("tile_lanes", ctypes.c_int), ("tile_splits", ctypes.c_int),
+                ("tile_block", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class zmc_scan_out(ctypes.Structure):
+    _fields_ = [("mean", _dp), ("err", _dp), ("errw", _dp), ("s1", _dp), ("s2", _dp),
+                ("tile_lanes", ctypes.c_int), ("tile_splits", ctypes.c_int),
+                ("tile_block", ctypes.c_int), ("launches", ctypes.c_int),
+                ("h2d_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
+                ("finalize_ms", ctypes.c_float), ("d2h_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float)]
+
+
+class zmc_integrand_info(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int), ("name", ctypes.c_char * 32),
+                ("m_rule", ctypes.c_int)]
+
+
+class zmc_device_info(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("sm_count", ctypes.c_int),
+                ("cc_major", ctypes.c_int), ("cc_minor", ctypes.c_int),
+                ("max_threads_per_sm", ctypes.c_int), ("clock_khz", ctypes.c_int),
+                ("total_mem", ctypes.c_size_t), ("name", ctypes.c_char * 96)]
+
+
+class zmc_pipe_result(ctypes.Structure):
+    _fields_ = [("pipe", ctypes.c_int), ("ops_per_clk_per_sm", ctypes.c_double),
+                ("ops_per_s", ctypes.c_double), ("clock_mhz", ctypes.c_double),
+                ("ms", ctypes.c_double), ("ops", ctypes.c_int64)]
+
+
+PIPE_NAMES = ["FFMA", "IMAD", "IMAD.WIDE", "IMAD.HI", "LOP3", "SHF", "MUFU.RSQ",
+              "MUFU.EX2+LG2", "DFMA", "PHILOX_CALL", "MUFU.EX2", "MUFU.COS"]
+
+# (name, restype, argtypes) of every exported entry point this binding uses.
+SIGNATURES = [
+    ("zmc_version", ctypes.c_int, []),
+    ("zmc_last_error", ctypes.c_char_p, []),
+    ("zmc_scan_desc_init", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc)]),
+    ("zmc_integrand_info_get", ctypes.c_int, [ctypes.c_int,
+                                              ctypes.POINTER(zmc_integrand_info)]),
+    ("zmc_device_info_get", ctypes.c_int, [ctypes.POINTER(zmc_device_info)]),
+    ("zmc_validate", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc)]),
+    ("zmc_workspace_size", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc),
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+    ("zmc_scan", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int,
+                                _i64p, _dp, ctypes.c_int64, ctypes.c_int,
+                                ctypes.c_uint64, _dp, _dp]),
+    ("zmc_scan_ex", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc),
+                                   ctypes.POINTER(zmc_scan_out)]),
+    ("zmc_stream_words", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_uint64, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_uint32)]),
+    ("zmc_pipe_measure", ctypes.c_int, [ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(zmc_pipe_result)]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIBRARY):
+    """Load libzmc.so (built by __graft_entry__.build()); raise if missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(
+                "libzmc.so is not built (%s); run __graft_entry__.build() — "
+                "there is no CPU fallback" % path)
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != ZMC_OK:
+        raise ZmcError(rc, load().zmc_last_error().decode(errors="replace"))
+
+
+# ------------------------------------------------------- same-name wrappers --
+def zmc_version() -> int:
+    return load().zmc_version()
+
+
+def zmc_last_error() -> str:
+    return load().zmc_last_error().decode(errors="replace")
+
+
+def zmc_scan_desc_init() -> zmc_scan_desc:
+    d = zmc_scan_desc()
+    _check(load().zmc_scan_desc_init(ctypes.byref(d)))
+    return d
+
+
+def zmc_integrand_info_get(gid: int) -> zmc_integrand_info:
+    info = zmc_integrand_info()
+    _check(load().zmc_integrand_info_get(gid, ctypes.byref(info)))
+    return info
+
+
+def zmc_device_info_get() -> zmc_device_info:
+    info = zmc_device_info()
+    _check(load().zmc_device_info_get(ctypes.byref(info)))
+    return info
+
+
+def zmc_validate(d: zmc_scan_desc) -> int:
+    return load().zmc_validate(ctypes.byref(d))
+
+
+def zmc_workspace_size(d: zmc_scan_desc) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().zmc_workspace_size(ctypes.byref(d), ctypes.byref(n)))
+    return int(n.value)
+
+
+def zmc_scan(gid, N, lo, hi, lengths, values, S, T, seed):
+    """The simple host entry point; returns (mean, err) numpy arrays."""
+    lo = np.ascontiguousarray(lo, np.float64)
+    hi = np.ascontiguousarray(hi, np.float64)
+    L = np.ascontiguousarray(lengths, np.int64)
+    v = np.ascontiguousarray(values, np.float64)
+    P = int(np.prod(L))
+    mean = np.empty(P)
+    err = np.empty(P)
+    _check(load().zmc_scan(int(gid), int(N), lo.ctypes.data_as(_dp), hi.ctypes.data_as(_dp),
+                           len(L), L.ctypes.data_as(_i64p), v.ctypes.data_as(_dp),
+                           int(S), int(T), int(seed), mean.ctypes.data_as(_dp),
+                           err.ctypes.data_as(_dp)))
+    return mean, err
+
+
+def zmc_scan_ex(d: zmc_scan_desc, o: zmc_scan_out) -> zmc_scan_out:
+    _check(load().zmc_scan_ex(ctypes.byref(d), ctypes.byref(o)))
+    return o
+
+
+def zmc_stream_words(seed: int, p: int, t: int, first_word: int, nwords: int) -> np.ndarray:
+    out = np.zeros(nwords, dtype=np.uint32)
+    _check(load().zmc_stream_words(int(seed), int(p), int(t), int(first_word), int(nwords),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    return out
+
+
+def zmc_pipe_measure(pipe: int, iterations: int = 4096) -> zmc_pipe_result:
+    r = zmc_pipe_result()
+    _check(load().zmc_pipe_measure(int(pipe), int(iterations), ctypes.byref(r)))
+    return r
+
+
+# -------------------------------------------------------------- helpers --
+class _Keep:
+    """Holds numpy buffers alive while a descriptor points into them."""
+
+    def __init__(self):
+        self.items = []
+
+    def arr(self, a, dtype):
+        a = np.ascontiguousarray(a, dtype)
+        self.items.append(a)
+        return a
+
+
+def make_desc(gid, N, lo, hi, lengths, values=None, S=1, T=1, seed=0,
+              precision=ZMC_FP32_KAHAN, mem=ZMC_MEM_HOST, first_index=0, count=-1,
+              stream=None, tiles=(0, 0, 0), flags=0, keep=None):
+    """Fill a zmc_scan_desc.  For ZMC_MEM_DEVICE, ``values`` is a device
+    pointer (int) or a torch CUDA float64 tensor."""
+    keep = keep if keep is not None else _Keep()
+    d = zmc_scan_desc_init()
+    lo_a = keep.arr(lo, np.float64)
+    hi_a = keep.arr(hi, np.float64)
+    L = keep.arr(lengths, np.int64)
+    d.integrand_id, d.N, d.M = int(gid), int(N), len(L)
+    d.lo, d.hi = lo_a.ctypes.data_as(_dp), hi_a.ctypes.data_as(_dp)
+    d.list_len = L.ctypes.data_as(_i64p)
+    if mem == ZMC_MEM_HOST:
+        v = keep.arr(values, np.float64)
+        d.list_vals = v.ctypes.data_as(_dp)
+    else:
+        ptr = values if isinstance(values, int) else values.data_ptr()
+        keep.items.append(values)
+        d.list_vals = ctypes.cast(ctypes.c_void_p(ptr), _dp)
+    d.samples_per_point, d.trials, d.seed = int(S), int(T), int(seed) & (2 ** 64 - 1)
+    d.precision, d.mem = int(precision), int(mem)
+    d.first_index, d.count = int(first_index), int(count)
+    d.stream = stream
+    d.tile_lanes, d.tile_splits, d.tile_block = (int(x) for x in tiles)
+    d.flags = int(flags)
+    return d, keep
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(_dp)
+    return ctypes.cast(ctypes.c_void_p(x.data_ptr()), _dp)
+
+
+def scan(gid, N, lo, hi, lengths, values, S, T, seed, precision=ZMC_FP32_KAHAN,
+         first_index=0, count=-1, tiles=(0, 0, 0), flags=0, want_sums=False,
+         want_errw=True):
+    """Host-memory scan through zmc_scan_ex; returns a dict of numpy arrays
+    (mean, err, errw, [s1, s2]) and the zmc_scan_out."""
+    d, keep = make_desc(gid, N, lo, hi, lengths, values, S, T, seed, precision,
+                        ZMC_MEM_HOST, first_index, count, None, tiles, flags)
+    P = int(np.prod(np.asarray(lengths, np.int64)))
+    n = (P - first_index) if count < 0 else count
+    res = {"mean": np.empty(n), "err": np.empty(n)}
+    if want_errw:
+        res["errw"] = np.empty(n)
+    if want_sums:
+        res["s1"] = np.empty((n, T))
+        res["s2"] = np.empty((n, T))
+    o = zmc_scan_out()
+    o.mean, o.err = _ptr(res["mean"]), _ptr(res["err"])
+    o.errw = _ptr(res.get("errw"))
+    o.s1, o.s2 = _ptr(res.get("s1")), _ptr(res.get("s2"))
+    zmc_scan_ex(d, o)
+    return res, o
+
+
+def scan_device(gid, N, lo, hi, lengths, values_dev, S, T, seed, out_mean, out_err,
+                out_errw=None, out_s1=None, out_s2=None, precision=ZMC_FP32_KAHAN,
+                first_index=0, count=-1, stream=None, workspace=None, tiles=(0, 0, 0),
+                flags=0):
+    """Device-memory scan: values and outputs are torch CUDA float64 tensors;
+    work is enqueued on ``stream`` (a cudaStream_t as int, or None)."""
+    d, keep = make_desc(gid, N, lo, hi, lengths, values_dev, S, T, seed, precision,
+                        ZMC_MEM_DEVICE, first_index, count, stream, tiles, flags)
+    if workspace is not None:
+        d.workspace = ctypes.c_void_p(workspace.data_ptr())
+        d.workspace_bytes = workspace.numel() * workspace.element_size()
+    o = zmc_scan_out()
+    o.mean, o.err = _ptr(out_mean), _ptr(out_err)
+    o.errw, o.s1, o.s2 = _ptr(out_errw), _ptr(out_s1), _ptr(out_s2)
+    zmc_scan_ex(d, o)
+    return o
