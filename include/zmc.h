@@ -238,6 +238,32 @@ int zmc_scan_ex(const zmc_scan_desc* d, zmc_scan_out* o);
 int zmc_stream_words(uint64_t seed, int64_t p, int t, uint64_t first_word,
                      int64_t nwords, uint32_t* out);
 
+/*
+ * A scan that allocates nothing.  The paper has no counterpart: this serves
+ * callers that cannot call cudaMalloc (or any allocator) when they scan —
+ * code on a latency-critical path, where an allocation can wait on the
+ * driver or synchronise the device; code inside a host framework that owns
+ * all device memory through its own allocator and budget; hosts that fix
+ * their device footprint at start-up.
+ *
+ * Same computation, kernels and results as zmc_scan_ex.  d->mem must be
+ * ZMC_MEM_DEVICE (lists and outputs in caller-owned device memory),
+ * d->workspace NULL, and ZMC_F_TIMINGS unset; ZMC_F_SYNC is honoured.  Work
+ * is enqueued on d->stream (NULL = the CUDA default stream).
+ *
+ * Scratch: the FP64 partial sums live in a file-scope device array of
+ * ZMC_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the library
+ * holds until the process exits.  A call whose partial sums
+ * (points x trials x sample splits x 16 bytes) exceed it returns ZMC_EINVAL
+ * with a message; scan a smaller slice (first_index, count) per call.  The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * nothing in it needs clearing, but calls that overlap on the GPU race on it.
+ */
+#define ZMC_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int zmc_scan_noalloc(const zmc_scan_desc* d, zmc_scan_out* o);
+
 #ifdef __cplusplus
 }
 #endif

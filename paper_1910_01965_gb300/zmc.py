@@ -106,6 +106,8 @@ SIGNATURES = [
                                         ctypes.POINTER(ctypes.c_uint32)]),
     ("zmc_pipe_measure", ctypes.c_int, [ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(zmc_pipe_result)]),
+    ("zmc_scan_noalloc", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc),
+                                        ctypes.POINTER(zmc_scan_out)]),
 ]
 
 _lock = threading.Lock()
@@ -205,6 +207,16 @@ def zmc_pipe_measure(pipe: int, iterations: int = 4096) -> zmc_pipe_result:
     r = zmc_pipe_result()
     _check(load().zmc_pipe_measure(int(pipe), int(iterations), ctypes.byref(r)))
     return r
+
+
+ZMC_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def zmc_scan_noalloc(d: zmc_scan_desc, o: zmc_scan_out) -> zmc_scan_out:
+    """The scan entry point that allocates nothing (device-memory lists and
+    outputs; scratch is the library's fixed 16 MiB device array)."""
+    _check(load().zmc_scan_noalloc(ctypes.byref(d), ctypes.byref(o)))
+    return o
 
 
 # -------------------------------------------------------------- helpers --
