@@ -146,23 +146,26 @@ def bench_workload(name: str):
             "cosprod_100": wl.scan_cosprod_100}[name]()
 
 
-def traffic_per_launch(spec, n_unit_splits: int):
-    """DRAM bytes of one sampling-kernel launch from the committed ncu summary,
-    scaled by unit-splits; None when the kernel sources changed since."""
+def traffic_per_launch(spec):
+    """DRAM bytes (read + write) of one sampling-kernel launch from the
+    committed ncu summary; None when the kernel sources changed since the
+    counters were taken.  The summary's figure comes from the 10^5-point cut
+    of the same workload: the partial sums (16 B per unit) stay in L2 for both
+    grid sizes, so the DRAM bytes do not grow with the grid."""
     from paper_1910_01965_gb300 import build as B
     path = os.path.join(ROOT, "profiles", "scan_kernel_gauss03_N4_fp32k.md")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or spec.integrand_id != 2 or spec.N != 4:
         return None
     stamp = B.source_stamp()
-    per_us, src = None, None
+    val, src = None, None
     for line in open(path):
-        if line.startswith("traffic_bytes_per_unit_split:"):
-            per_us = float(line.split(":", 1)[1].split()[0])
+        if line.startswith("traffic_bytes_per_launch:"):
+            val = float(line.split(":", 1)[1].split()[0])
         if line.startswith("kernel_source_stamp:"):
             src = line.split(":", 1)[1].strip()
-    if per_us is None or src != stamp:
+    if val is None or src != stamp:
         return None
-    return per_us * n_unit_splits
+    return val
 
 
 # ------------------------------------------------------------- CPU oracle --
@@ -322,7 +325,7 @@ def main():
     peak = info.sm_count * 128 * f_max * 1e6 / 1e12   # lane-ops per second, T
     achieved = ops / (k_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": traffic_per_launch(spec, n_us),
+                "frac": achieved / peak, "traffic": traffic_per_launch(spec),
                 "kernel": "scan_kernel (sampling)", "kernel_ms": k_ms,
                 "ops_per_eval": ops_per_eval(spec.integrand_id, spec.N, prec),
                 "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s)" % (
