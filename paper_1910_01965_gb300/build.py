@@ -41,9 +41,12 @@ def _units():
         for gid in range(6):
             units.append(("scan_p%d_g%d.o" % (prec, gid), "zmc_scan_inst.cu",
                           ["-DZMC_INST_PREC=%d" % prec, "-DZMC_INST_GID=%d" % gid]))
+    for prec in range(3):
+        units.append(("batch_p%d.o" % prec, "zmc_batch_inst.cu",
+                      ["-DZMC_INST_PREC=%d" % prec]))
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         name = os.path.basename(src)
-        if name == "zmc_scan_inst.cu":
+        if name in ("zmc_scan_inst.cu", "zmc_batch_inst.cu"):
             continue
         units.append((name.replace(".cu", ".o"), name, []))
     return units

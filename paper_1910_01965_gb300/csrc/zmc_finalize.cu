@@ -16,9 +16,7 @@
 
 namespace zmc {
 
-__global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.count) return;
+__device__ __forceinline__ void finalize_point(const FinalizeArgs& a, int64_t i) {
   const double S = static_cast<double>(a.S);
   const double* part = a.partial + 2 * (i * a.T) * a.splits;
   double sumI = 0.0, pooled = 0.0;
@@ -49,6 +47,34 @@ __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
   a.err[i] = a.T > 1 ? sqrt(dev2 / (static_cast<double>(a.T) * (a.T - 1))) : NAN;
   if (a.errw)
     a.errw[i] = a.S > 1 ? a.V * sqrt(pooled / a.T / (static_cast<double>(a.T) * S)) : NAN;
+}
+
+__global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < a.count) finalize_point(a, i);
+}
+
+// Every point of every scan of a batch: thread i finds its scan by binary
+// search over the prefix array (consecutive threads on consecutive points of
+// one scan, so writes stay coalesced).
+__global__ void finalize_batch_kernel(const __grid_constant__ FinalizeBatchArgs b) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= b.total) return;
+  int lo = 0, hi = b.nscans - 1;
+  while (lo < hi) {  // the last scan whose prefix is <= i
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.prefix[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  finalize_point(b.fa[lo], i - b.prefix[lo]);
+}
+
+int finalize_batch_launch(const FinalizeBatchArgs& a, void* stream) {
+  if (a.total <= 0) return 0;
+  const int block = 256;
+  const int64_t grid = (a.total + block - 1) / block;
+  finalize_batch_kernel<<<static_cast<unsigned>(grid), block, 0,
+                          static_cast<cudaStream_t>(stream)>>>(a);
+  return static_cast<int>(cudaGetLastError());
 }
 
 int finalize_launch(const FinalizeArgs& a, void* stream) {

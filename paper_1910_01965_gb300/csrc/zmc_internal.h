@@ -35,6 +35,8 @@ struct ScanArgs {
   int32_t nvals;        // total list length
   int32_t stage_smem;   // 1: lists copied to shared memory first
   int32_t idx32;        // 1: every flat index of the slice is below 2^32
+  int32_t gid;          // integrand id (batched launches dispatch on it)
+  int32_t N;            // dimension
   const double* vals;   // device, the M lists concatenated
   int64_t len[ZMC_MAX_M];
   int32_t off[ZMC_MAX_M];
@@ -71,6 +73,35 @@ typedef int (*ScanLaunchFn)(const ScanArgs& a, int block, int64_t grid,
 
 ScanLaunchFn scan_launcher(int precision, int integrand, int N);
 int finalize_launch(const FinalizeArgs& a, void* stream);
+
+// ------------------------------------------------------------- batches --
+// One tile = the unit-splits one block sums at once, all of one scan.
+struct BatchTile {
+  int32_t scan;      // index into the batch's ScanArgs array
+  int32_t units;     // unit-splits in this tile (<= block / lanes)
+  int64_t first_us;  // first unit-split of the tile
+};
+
+struct BatchArgs {
+  const ScanArgs* scans;          // [nscans], device
+  const BatchTile* tiles;         // [ntiles], device, in the order they are taken
+  int64_t ntiles;
+  unsigned long long* counter;    // device; zeroed before each launch
+};
+
+struct FinalizeBatchArgs {
+  const FinalizeArgs* fa;   // [nscans], device
+  const int64_t* prefix;    // [nscans + 1], device: first flat output index of each scan
+  int32_t nscans;
+  int64_t total;            // prefix[nscans]
+};
+
+// Launch the persistent batched sampling kernel of one precision.
+int batch_launch(int precision, const BatchArgs& b, int grid, int block, size_t smem,
+                 void* stream);
+// Blocks of the batched kernel that fit on one SM at `block` threads, `smem` bytes.
+int batch_blocks_per_sm(int precision, int block, size_t smem, int* out);
+int finalize_batch_launch(const FinalizeBatchArgs& a, void* stream);
 
 int stream_words_launch(uint64_t seed, int64_t p, int t, uint64_t first_word,
                         int64_t nwords, uint32_t* out_dev, void* stream);

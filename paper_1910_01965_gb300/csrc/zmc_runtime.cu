@@ -289,6 +289,8 @@ void fill_scan_args(const zmc_scan_desc* d, int64_t count, const TilePlan& tp,
   }
   fill_round_keys(d->seed, a->rk0, a->rk1);
   a->partial = partial_dev;
+  a->gid = d->integrand_id;
+  a->N = d->N;
 }
 
 int launch_scan_args(const zmc_scan_desc* d, const ScanArgs& a, const TilePlan& tp,

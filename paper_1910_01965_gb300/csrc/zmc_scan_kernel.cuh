@@ -196,9 +196,11 @@ __device__ __forceinline__ const void* stage_lists(const ScanArgs& a, double* sm
 
 // Sum over the sample groups [q, q_end) with stride `step` (one lane).
 template <int N, class F, int PREC>
-__device__ __forceinline__ void lane_groups(const ScanArgs& a, const PhiloxUnit& pu,
-                                            const F& f, uint32_t q, uint32_t q_end,
-                                            uint32_t step, LaneAcc<PREC>& acc) {
+__device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
+                                            const uint32_t* __restrict__ rk1,
+                                            const PhiloxUnit& pu, const F& f, uint32_t q,
+                                            uint32_t q_end, uint32_t step,
+                                            LaneAcc<PREC>& acc) {
   constexpr int G = group_samples(N);
   constexpr int C = group_calls(N);
   // Two groups in flight give each lane two independent Philox chains; for
@@ -219,7 +221,7 @@ __device__ __forceinline__ void lane_groups(const ScanArgs& a, const PhiloxUnit&
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          philox_call_pre(pu, a.rk0, a.rk1, sp[c].hi, sp[c].lo, &r[u][4 * c]);
+          philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[u][4 * c]);
           sp[c].advance();
         }
       if constexpr (U == 1) {
@@ -233,7 +235,7 @@ __device__ __forceinline__ void lane_groups(const ScanArgs& a, const PhiloxUnit&
     if (q < q_end) {
       uint32_t r[4 * C];
 #pragma unroll
-      for (int c = 0; c < C; ++c) philox_call_pre(pu, a.rk0, a.rk1, sp[c].hi, sp[c].lo, &r[4 * c]);
+      for (int c = 0; c < C; ++c) philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[4 * c]);
 #pragma unroll
       for (int g = 0; g < G; ++g) acc.add(f.eval(&r[g * N]));
     }
@@ -243,7 +245,7 @@ __device__ __forceinline__ void lane_groups(const ScanArgs& a, const PhiloxUnit&
       uint32_t r[4 * C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        philox_call_pre(pu, a.rk0, a.rk1, sp[c].hi, sp[c].lo, &r[4 * c]);
+        philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[4 * c]);
         sp[c].advance();
       }
 #pragma unroll
@@ -254,22 +256,26 @@ __device__ __forceinline__ void lane_groups(const ScanArgs& a, const PhiloxUnit&
 
 // The ragged last group of a unit when G does not divide S.
 template <int N, class F, int PREC>
-__device__ __forceinline__ void lane_tail_group(const ScanArgs& a, const PhiloxUnit& pu,
-                                                const F& f, uint32_t q, int valid,
-                                                LaneAcc<PREC>& acc) {
+__device__ __forceinline__ void lane_tail_group(const uint32_t* __restrict__ rk0,
+                                                const uint32_t* __restrict__ rk1,
+                                                const PhiloxUnit& pu, const F& f, uint32_t q,
+                                                int valid, LaneAcc<PREC>& acc) {
   constexpr int G = group_samples(N);
   constexpr int C = group_calls(N);
   uint32_t r[4 * C];
 #pragma unroll
-  for (int c = 0; c < C; ++c) philox_call(pu, a.rk0, a.rk1, q * C + c, &r[4 * c]);
+  for (int c = 0; c < C; ++c) philox_call(pu, rk0, rk1, q * C + c, &r[4 * c]);
 #pragma unroll
   for (int g = 0; g < G; ++g)
     if (g < valid) acc.add(f.eval(&r[g * N]));
 }
 
 // Work of one lane for unit-split `us`: decode, prepare, sample, sum.
+// rk0/rk1 are the ten Philox round keys (parameter space in the single-scan
+// kernel, registers in the batched one).
 template <int N, class F, int PREC>
-__device__ __forceinline__ void unit_split_lane(const ScanArgs& a, const void* table,
+__device__ __forceinline__ void unit_split_lane(const ScanArgs& a, const uint32_t* rk0,
+                                                const uint32_t* rk1, const void* table,
                                                 const float* dimc, int64_t us, int lane,
                                                 LaneAcc<PREC>& acc) {
   constexpr int G = group_samples(N);
@@ -291,19 +297,19 @@ __device__ __forceinline__ void unit_split_lane(const ScanArgs& a, const void* t
       for (int g = 0; g < cnt; ++g) acc.add(f.eval(nullptr));
     }
   } else {
-    const PhiloxUnit pu = philox_unit(a.rk0, a.rk1, static_cast<uint64_t>(p), t);
+    const PhiloxUnit pu = philox_unit(rk0, rk1, static_cast<uint64_t>(p), t);
     const int64_t q0 = split * a.gps;
     const int64_t q1 = min(q0 + a.gps, a.ngroups);
     const int64_t nfull = a.S / G;
     const int64_t qf = min(q1, nfull);
     if (q0 + lane < qf)
-      lane_groups<N, F, PREC>(a, pu, f, static_cast<uint32_t>(q0 + lane),
+      lane_groups<N, F, PREC>(rk0, rk1, pu, f, static_cast<uint32_t>(q0 + lane),
                               static_cast<uint32_t>(qf), static_cast<uint32_t>(a.lanes),
                               acc);
     if (G > 1) {
       const int valid = static_cast<int>(a.S - nfull * G);
       if (valid > 0 && nfull >= q0 && nfull < q1 && ((nfull - q0) & (a.lanes - 1)) == lane)
-        lane_tail_group<N, F, PREC>(a, pu, f, static_cast<uint32_t>(nfull), valid, acc);
+        lane_tail_group<N, F, PREC>(rk0, rk1, pu, f, static_cast<uint32_t>(nfull), valid, acc);
     }
   }
 }
@@ -349,7 +355,7 @@ scan_kernel(const __grid_constant__ ScanArgs a) {
   const int64_t us = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> a.lanes_log2) +
                      (threadIdx.x >> a.lanes_log2);
   LaneAcc<PREC> acc;
-  if (us < a.n_us) unit_split_lane<N, F, PREC>(a, table, dimc, us, lane, acc);
+  if (us < a.n_us) unit_split_lane<N, F, PREC>(a, a.rk0, a.rk1, table, dimc, us, lane, acc);
   double s1 = acc.sum1(), s2 = acc.sum2();
   reduce_unit_split(a, s1, s2, red);
   if (lane == 0 && us < a.n_us) {

@@ -82,6 +82,16 @@ class zmc_pipe_result(ctypes.Structure):
                 ("ms", ctypes.c_double), ("ops", ctypes.c_int64)]
 
 
+class zmc_batch_info(ctypes.Structure):
+    _fields_ = [("scans", ctypes.c_int), ("precisions", ctypes.c_int),
+                ("tiles", ctypes.c_int64), ("evaluations", ctypes.c_int64),
+                ("grid", ctypes.c_int), ("block", ctypes.c_int),
+                ("scratch_bytes", ctypes.c_size_t), ("graph", ctypes.c_int),
+                ("launches_per_run", ctypes.c_int)]
+
+
+ZMC_BATCH_GRAPH = 1
+
 PIPE_NAMES = ["FFMA", "IMAD", "IMAD.WIDE", "IMAD.HI", "LOP3", "SHF", "MUFU.RSQ",
               "MUFU.EX2+LG2", "DFMA", "PHILOX_CALL", "MUFU.EX2", "MUFU.COS"]
 
@@ -108,6 +118,14 @@ SIGNATURES = [
                                         ctypes.POINTER(zmc_pipe_result)]),
     ("zmc_scan_noalloc", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc),
                                         ctypes.POINTER(zmc_scan_out)]),
+    ("zmc_batch_create", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc),
+                                        ctypes.POINTER(zmc_scan_out), ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("zmc_batch_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("zmc_batch_info_get", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(zmc_batch_info)]),
+    ("zmc_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("zmc_scan_batch", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc), ctypes.c_int,
+                                      ctypes.POINTER(zmc_scan_out)]),
 ]
 
 _lock = threading.Lock()
@@ -217,6 +235,44 @@ def zmc_scan_noalloc(d: zmc_scan_desc, o: zmc_scan_out) -> zmc_scan_out:
     outputs; scratch is the library's fixed 16 MiB device array)."""
     _check(load().zmc_scan_noalloc(ctypes.byref(d), ctypes.byref(o)))
     return o
+
+
+def zmc_batch_create(descs, outs, flags=0):
+    """descs, outs: ctypes arrays (or lists) of zmc_scan_desc / zmc_scan_out.
+    Returns the opaque batch handle (int)."""
+    n = len(descs)
+    D = (zmc_scan_desc * n)(*descs)
+    O = (zmc_scan_out * n)(*outs)
+    h = ctypes.c_void_p()
+    _check(load().zmc_batch_create(D, O, n, int(flags), ctypes.byref(h)))
+    for i in range(n):
+        outs[i].tile_lanes, outs[i].tile_splits = O[i].tile_lanes, O[i].tile_splits
+        outs[i].tile_block = O[i].tile_block
+    return h.value
+
+
+def zmc_batch_run(handle, stream=None):
+    _check(load().zmc_batch_run(ctypes.c_void_p(handle), stream))
+
+
+def zmc_batch_info_get(handle) -> zmc_batch_info:
+    info = zmc_batch_info()
+    _check(load().zmc_batch_info_get(ctypes.c_void_p(handle), ctypes.byref(info)))
+    return info
+
+
+def zmc_batch_destroy(handle):
+    _check(load().zmc_batch_destroy(ctypes.c_void_p(handle)))
+
+
+def zmc_scan_batch(descs, outs):
+    n = len(descs)
+    D = (zmc_scan_desc * n)(*descs)
+    O = (zmc_scan_out * n)(*outs)
+    _check(load().zmc_scan_batch(D, n, O))
+    for i in range(n):
+        outs[i] = O[i]
+    return outs
 
 
 # -------------------------------------------------------------- helpers --
