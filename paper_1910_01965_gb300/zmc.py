@@ -92,6 +92,23 @@ class zmc_batch_info(ctypes.Structure):
 
 ZMC_BATCH_GRAPH = 1
 
+
+class zmc_server_opts(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("step_ms", ctypes.c_double),
+                ("chunk_units", ctypes.c_int64), ("fail_alloc_every", ctypes.c_int)]
+
+
+class zmc_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("max_queued", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("evaluations", ctypes.c_int64), ("busy_ms", ctypes.c_double),
+                ("evals_per_s", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mem_in_use", ctypes.c_size_t),
+                ("mem_peak", ctypes.c_size_t)]
+
 PIPE_NAMES = ["FFMA", "IMAD", "IMAD.WIDE", "IMAD.HI", "LOP3", "SHF", "MUFU.RSQ",
               "MUFU.EX2+LG2", "DFMA", "PHILOX_CALL", "MUFU.EX2", "MUFU.COS"]
 
@@ -126,6 +143,19 @@ SIGNATURES = [
     ("zmc_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("zmc_scan_batch", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc), ctypes.c_int,
                                       ctypes.POINTER(zmc_scan_out)]),
+    ("zmc_server_opts_init", ctypes.c_int, [ctypes.POINTER(zmc_server_opts)]),
+    ("zmc_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(zmc_server_opts),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    ("zmc_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(zmc_scan_desc),
+                                  ctypes.POINTER(zmc_scan_out),
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    ("zmc_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
+                                ctypes.POINTER(ctypes.c_int)]),
+    ("zmc_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]),
+    ("zmc_cancel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("zmc_server_stats_get", ctypes.c_int, [ctypes.c_void_p,
+                                            ctypes.POINTER(zmc_server_stats)]),
+    ("zmc_server_destroy", ctypes.c_int, [ctypes.c_void_p]),
 ]
 
 _lock = threading.Lock()
@@ -273,6 +303,100 @@ def zmc_scan_batch(descs, outs):
     for i in range(n):
         outs[i] = O[i]
     return outs
+
+
+def zmc_server_opts_init() -> zmc_server_opts:
+    o = zmc_server_opts()
+    _check(load().zmc_server_opts_init(ctypes.byref(o)))
+    return o
+
+
+def zmc_server_create(budget_bytes: int, opts: zmc_server_opts = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().zmc_server_create(int(budget_bytes),
+                                    ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(h)))
+    return h.value
+
+
+def zmc_submit(server: int, d: zmc_scan_desc, o: zmc_scan_out) -> int:
+    t = ctypes.c_uint64()
+    _check(load().zmc_submit(ctypes.c_void_p(server), ctypes.byref(d), ctypes.byref(o),
+                             ctypes.byref(t)))
+    return int(t.value)
+
+
+def zmc_poll(server: int, ticket: int) -> bool:
+    done = ctypes.c_int()
+    _check(load().zmc_poll(ctypes.c_void_p(server), int(ticket), ctypes.byref(done)))
+    return bool(done.value)
+
+
+def zmc_wait(server: int, ticket: int, timeout_ms: int = -1) -> int:
+    """Returns the request's final status code (ZMC_OK, ZMC_ECANCELED, ...)
+    or ZMC_ETIMEDOUT; raises only for an unknown ticket."""
+    rc = load().zmc_wait(ctypes.c_void_p(server), int(ticket), int(timeout_ms))
+    if rc == ZMC_ENOTFOUND:
+        _check(rc)
+    return rc
+
+
+def zmc_cancel(server: int, ticket: int) -> int:
+    return load().zmc_cancel(ctypes.c_void_p(server), int(ticket))
+
+
+def zmc_server_stats_get(server: int) -> zmc_server_stats:
+    st = zmc_server_stats()
+    _check(load().zmc_server_stats_get(ctypes.c_void_p(server), ctypes.byref(st)))
+    return st
+
+
+def zmc_server_destroy(server: int):
+    _check(load().zmc_server_destroy(ctypes.c_void_p(server)))
+
+
+class Server:
+    """Keeps each request's descriptor and host output arrays alive until the
+    caller has collected them (marshalling only; the loop is the library's)."""
+
+    def __init__(self, budget_bytes: int, **opts):
+        o = zmc_server_opts_init()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.handle = zmc_server_create(budget_bytes, o)
+        self.requests = {}
+
+    def submit(self, gid, N, lo, hi, lengths, values, S, T, seed, precision=ZMC_FP32_KAHAN,
+               first_index=0, count=-1, tiles=(0, 0, 0), want_sums=False):
+        d, keep = make_desc(gid, N, lo, hi, lengths, values, S, T, seed, precision,
+                            ZMC_MEM_HOST, first_index, count, None, tiles)
+        P = int(np.prod(np.asarray(lengths, np.int64)))
+        n = (P - first_index) if count < 0 else count
+        res = {"mean": np.empty(n), "err": np.empty(n), "errw": np.empty(n)}
+        if want_sums:
+            res["s1"] = np.empty((n, T))
+            res["s2"] = np.empty((n, T))
+        o = zmc_scan_out()
+        o.mean, o.err, o.errw = _ptr(res["mean"]), _ptr(res["err"]), _ptr(res["errw"])
+        o.s1, o.s2 = _ptr(res.get("s1")), _ptr(res.get("s2"))
+        t = zmc_submit(self.handle, d, o)
+        self.requests[t] = (d, o, res, keep)
+        return t
+
+    def wait(self, ticket, timeout_ms=-1):
+        return zmc_wait(self.handle, ticket, timeout_ms)
+
+    def result(self, ticket):
+        d, o, res, keep = self.requests[ticket]
+        return res, o
+
+    def stats(self):
+        return zmc_server_stats_get(self.handle)
+
+    def close(self):
+        if self.handle:
+            zmc_server_destroy(self.handle)
+            self.handle = None
 
 
 # -------------------------------------------------------------- helpers --
