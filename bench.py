@@ -119,19 +119,13 @@ def dist_setup():
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_1910_01965_gb300 import shard
+    shard.barrier()
 
 
 def max_over_ranks(world, value: float) -> float:
-    if world == 1:
-        return value
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1910_01965_gb300 import shard
+    return shard.max_over_ranks(value)
 
 
 # -------------------------------------------------------------- workloads --
@@ -185,14 +179,15 @@ def cpu_oracle_run(spec, seconds: float, seed: int = 4242):
     npts = int(max(cores, min(spec.P, seconds * rate / per_point)))
     pts = wl.sample_points(spec.P, npts, seed=seed)
     t0 = time.perf_counter()
-    O.scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
-                  spec.samples, spec.trials, spec.seed, pts)
+    ref = O.scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                        spec.values, spec.samples, spec.trials, spec.seed, pts,
+                        want_sums=True)
     dt = time.perf_counter() - t0
     value = pts.size * per_point / dt
     desc = ("%d of %d grid points (seeded sample), all %d trials x %d samples each: "
             "%.3g evals in %.1f s" % (pts.size, spec.P, spec.trials, spec.samples,
                                       pts.size * per_point, dt))
-    return value, cores, desc, pts.size * per_point, dt
+    return value, cores, desc, pts, ref
 
 
 def run_reference(args, spec, world, rank):
@@ -239,6 +234,163 @@ def run_reference(args, spec, world, rank):
     return 0
 
 
+def accuracy(spec, pts, ref, got):
+    """Worst deviation of GPU results from the FP64 oracle over the sampled
+    points: scaled by max(|f|, V * RMS(g)) and in standard errors (errw)."""
+    V = float(np.prod(np.asarray(spec.hi) - np.asarray(spec.lo)))
+    R = V * np.sqrt(np.mean(ref["s2"], axis=1) / spec.samples)
+    scale = np.maximum(np.abs(ref["mean"]), R)
+    dm = np.abs(got["mean"][pts] - ref["mean"])
+    de = np.abs(got["err"][pts] - ref["err"])
+    se = ref["errw"]
+    return {"points": int(pts.size), "max_dmean_scaled": float(np.max(dm / scale)),
+            "max_dmean_stderr": float(np.max(dm / se)),
+            "max_derr_stderr": float(np.max(de / se))}
+
+
+def serving_run(window_s: float, rate: float = 500.0, large_fraction: float = 0.01,
+                budget=60 << 30):
+    """Open-loop Poisson arrivals through the library's serving loop; every
+    request is waited for.  Returns throughput and latency percentiles."""
+    from paper_1910_01965_gb300 import workloads as wl
+    from paper_1910_01965_gb300 import zmc
+    arr = wl.serving_poisson(rate=rate, window_s=window_s, large_fraction=large_fraction)
+    srv = zmc.Server(budget)
+    tickets = []
+    t0 = time.perf_counter()
+    try:
+        for a in arr:
+            now = time.perf_counter() - t0
+            if a.t > now:
+                time.sleep(a.t - now)
+            sp = a.spec
+            tickets.append((srv.submit(sp.integrand_id, sp.N, sp.lo, sp.hi, sp.lengths,
+                                       sp.values, sp.samples, sp.trials, sp.seed), a))
+        for t, a in tickets:
+            srv.wait(t)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        lat = {"small": [], "large": []}
+        for t, a in tickets:
+            lat["large" if a.large else "small"].append(srv.result(t)[1].total_ms)
+    finally:
+        srv.close()
+    evals = float(sum(a.spec.evals for t, a in tickets))
+    out = {"arrival_rate_per_s": rate, "window_s": window_s, "large_fraction": large_fraction,
+           "requests": len(tickets), "large_requests": len(lat["large"]),
+           "offered_evals_per_s": evals / window_s,
+           "evals_per_s": evals / wall, "gpu_busy_evals_per_s": st.evals_per_s,
+           "wall_s": wall, "steps": st.steps, "max_queued": st.max_queued,
+           "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mem_peak_bytes": st.mem_peak,
+           "budget_bytes": budget}
+    for k, v in lat.items():
+        if v:
+            out["%s_p50_ms" % k] = float(np.percentile(v, 50))
+            out["%s_p99_ms" % k] = float(np.percentile(v, 99))
+    return out
+
+
+def run_batch_bench(args, world, rank, local):
+    """One step = one run of the 256-scan uneven batch (persistent launch,
+    CUDA-graph replay); compared with the same scans as separate launches."""
+    import torch
+    from paper_1910_01965_gb300 import workloads as wl
+    from paper_1910_01965_gb300 import zmc
+    torch.cuda.set_device(local)
+    zmc.load()
+    specs = wl.batch_uneven_256()
+    prec = zmc.PRECISIONS[args.precision]
+    descs, outs, keep = [], [], []
+    for sp in specs:
+        vals = torch.tensor(sp.values, dtype=torch.float64, device="cuda")
+        d, k = zmc.make_desc(sp.integrand_id, sp.N, sp.lo, sp.hi, sp.lengths, vals, sp.samples,
+                             sp.trials, sp.seed, prec, mem=zmc.ZMC_MEM_DEVICE)
+        m = torch.empty(sp.P, dtype=torch.float64, device="cuda")
+        e = torch.empty_like(m)
+        o = zmc.zmc_scan_out()
+        o.mean, o.err = zmc._ptr(m), zmc._ptr(e)
+        descs.append(d)
+        outs.append(o)
+        keep.append((k, vals, m, e))
+    evals = float(sum(sp.evals for sp in specs))
+    ops = float(sum(ops_per_eval(sp.integrand_id, sp.N, prec) * sp.evals for sp in specs))
+    h = zmc.zmc_batch_create(descs, outs, zmc.ZMC_BATCH_GRAPH)
+    info = zmc.zmc_batch_info_get(h)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        zmc.zmc_batch_run(h, stream.cuda_stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        zmc.zmc_batch_run(h, stream.cuda_stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    zmc.zmc_batch_destroy(h)
+    # the same scans, one launch pair each
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for d, o in zip(descs, outs):
+        d.stream = stream.cuda_stream
+        zmc.zmc_scan_ex(d, o)
+    b.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b)
+    info_d = zmc.zmc_device_info_get()
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    f_max = json.load(open(peaks)).get("sm_max_mhz") if os.path.exists(peaks) else None
+    f_max = f_max or info_d.clock_khz / 1e3
+    peak = info_d.sm_count * 128 * f_max * 1e6 / 1e12
+    tot = sum(step_ms)
+    achieved = ops / (statistics.mean(step_ms) * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": evals * args.steps / (tot * 1e-3), "unit": "evals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec else "f64", "data": "synthetic",
+            "config": {"workload": "batch_uneven_256 (256 scans, one persistent launch per "
+                                   "precision, CUDA-graph replay)", "scans": len(specs),
+                       "tiles": int(info.tiles), "evaluations": evals,
+                       "precision": args.precision,
+                       "l2": "256 MiB buffer written between timed steps"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "batch_kernel (persistent)"},
+            "separate_launches": {"ms": seq_ms, "evals_per_s": evals / (seq_ms * 1e-3),
+                                  "launches": 2 * len(specs)},
+            "clocks": clk, "gpu_launches": info.launches_per_run * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving_bench(args, world, rank, local):
+    """The full serving workload: 500 req/s for a 10 s window, 1% large."""
+    import torch
+    from paper_1910_01965_gb300 import zmc
+    torch.cuda.set_device(local)
+    zmc.load()
+    clocks = ClockSampler(local)
+    clocks.start()
+    res = serving_run(args.serve_window, args.serve_rate, 0.01)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": res["evals_per_s"], "unit": "evals/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": res["wall_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serving_poisson (open loop, every request waited for)",
+                       "arrival_rate_per_s": args.serve_rate, "window_s": args.serve_window},
+            "serving": res, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------- main --
 def main():
     ap = argparse.ArgumentParser()
@@ -252,10 +404,26 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-window", type=float, default=1.0)
+    ap.add_argument("--serve-rate", type=float, default=500.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     world, rank, local = dist_setup()
+    if args.workload == "batch_uneven_256":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the reference arm times the oracle on the headline workload"}))
+            return 0
+        return run_batch_bench(args, world, rank, local)
+    if args.workload == "serving":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the reference arm times the oracle on the headline workload"}))
+            return 0
+        args.serve_window = 10.0 if args.serve_window == 1.0 else args.serve_window
+        return run_serving_bench(args, world, rank, local)
     spec = bench_workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, spec, world, rank)
@@ -353,9 +521,12 @@ def main():
            "steps": e2e_steps, "api": "zmc_scan_ex (ZMC_MEM_HOST, pinned host buffers)"}
 
     extra = {}
+    got = {"mean": mean.cpu().numpy(), "err": err.cpu().numpy()}
+    got64 = None
     if rank == 0 and not args.no_fp64 and prec != zmc.ZMC_FP64:
         step(zmc.ZMC_FP64, zmc.ZMC_F_SYNC)  # warm the FP64 kernel
         o64 = step(zmc.ZMC_FP64)
+        got64 = {"mean": mean.cpu().numpy(), "err": err.cpu().numpy()}
         fp64_v = spec.evals / (o64.total_ms * 1e-3)
         extra["fp64_path"] = {"value": fp64_v, "unit": "evals/s", "ms_per_step": o64.total_ms,
                               "kernel_ms": o64.kernel_ms,
@@ -363,8 +534,13 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, cores, desc, ev_n, dt = cpu_oracle_run(spec, args.cpu_seconds)
+        v, cores, desc, pts, ref = cpu_oracle_run(spec, args.cpu_seconds)
         cpu = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": desc}
+        extra["accuracy_vs_oracle"] = {args.precision: accuracy(spec, pts, ref, got)}
+        if got64 is not None:
+            extra["accuracy_vs_oracle"]["fp64"] = accuracy(spec, pts, ref, got64)
+    if rank == 0 and not args.no_serve:
+        extra["serving"] = serving_run(args.serve_window)
 
     if rank == 0:
         line = {

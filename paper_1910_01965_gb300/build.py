@@ -65,12 +65,18 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
+# The sources the single-scan sampling kernel is compiled from.
+KERNEL_SOURCES = ["zmc_scan_kernel.cuh", "zmc_integrands.cuh", "zmc_philox.cuh",
+                  "zmc_internal.h", "zmc_scan_inst.cu"]
+
+
 def source_stamp() -> str:
-    """Hash of the kernel and ABI sources alone (no flags, no machine): a
-    profile taken on the GPU machine stays valid here while this is unchanged."""
+    """Hash of the sampling kernel's sources alone (no flags, no machine): a
+    profile of that kernel taken on the GPU machine stays valid while this is
+    unchanged."""
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(CSRC, "*")) +
-                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    files = [os.path.join(CSRC, f) for f in KERNEL_SOURCES] + \
+        sorted(glob.glob(os.path.join(ROOT, "include", "zmc.h")))
     for f in files:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
