@@ -314,9 +314,34 @@ def run_batch_bench(args, world, rank, local):
         keep.append((k, vals, m, e))
     evals = float(sum(sp.evals for sp in specs))
     ops = float(sum(ops_per_eval(sp.integrand_id, sp.N, prec) * sp.evals for sp in specs))
+    stream = torch.cuda.current_stream()
+
+    def one_run_ms():
+        hh = zmc.zmc_batch_create(descs, outs, zmc.ZMC_BATCH_GRAPH)
+        zmc.zmc_batch_run(hh, stream.cuda_stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        zmc.zmc_batch_run(hh, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        zmc.zmc_batch_destroy(hh)
+        return a.elapsed_time(b)
+
+    untuned_ms = one_run_ms()
+    # the autotuner, once per scan class present (integrand, N, log2 S)
+    classes = {}
+    for sp, d in zip(specs, descs):
+        key = (sp.integrand_id, sp.N, int(np.log2(sp.samples)))
+        if key not in classes or sp.evals > classes[key][0].evals:
+            classes[key] = (sp, d)
+    t_tune = time.perf_counter()
+    tuned = 0
+    for key, (sp, d) in sorted(classes.items()):
+        zmc.zmc_autotune(d, args.tune_ms)
+        tuned += 1
+    tune_s = time.perf_counter() - t_tune
     h = zmc.zmc_batch_create(descs, outs, zmc.ZMC_BATCH_GRAPH)
     info = zmc.zmc_batch_info_get(h)
-    stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         zmc.zmc_batch_run(h, stream.cuda_stream)
@@ -364,7 +389,10 @@ def run_batch_bench(args, world, rank, local):
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "batch_kernel (persistent)"},
             "separate_launches": {"ms": seq_ms, "evals_per_s": evals / (seq_ms * 1e-3),
-                                  "launches": 2 * len(specs)},
+                                  "launches": 2 * len(specs), "tiles": "autotuned"},
+            "autotune": {"classes": tuned, "tune_s": tune_s,
+                         "untuned_batch_ms": untuned_ms,
+                         "untuned_evals_per_s": evals / (untuned_ms * 1e-3)},
             "clocks": clk, "gpu_launches": info.launches_per_run * args.steps}
     print(json.dumps(line), flush=True)
     return 0
@@ -407,6 +435,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-window", type=float, default=1.0)
     ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--tune-ms", type=int, default=300)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -50,6 +50,15 @@ TilePlan plan_batch_scan(const zmc_scan_desc* d) {
   const int G = group_samples(d->N);
   const int64_t Q = (d->samples_per_point + G - 1) / G;
   tp.block = kBatchBlock;
+  int tl = 0, tb = 0, tg = 0;
+  if (!d->tile_lanes && !d->tile_splits &&
+      tune_find(d->precision, d->integrand_id, d->N, d->samples_per_point, &tl, &tb, &tg)) {
+    // the autotuner's lanes and per-lane work; batches keep 256-thread blocks
+    tp.lanes = std::min(tl, kBatchBlock);
+    const int64_t per = int64_t(tp.lanes) * tg;
+    tp.splits = static_cast<int>(std::min<int64_t>(std::max<int64_t>(1, (Q + per - 1) / per), Q));
+    return tp;
+  }
   int lanes = d->tile_lanes;
   if (!lanes) {
     lanes = 32;
@@ -144,6 +153,7 @@ static bool device_ptr(const void* p) {
 
 int batch_create(const zmc_scan_desc* d, zmc_scan_out* o, int n, int flags, zmc_batch** out) {
   if (!out) return fail(ZMC_EINVAL, "out is NULL");
+  tune_ensure_loaded();
   if (n < 1 || !d || !o) return fail(ZMC_EINVAL, "a batch needs n >= 1 scans and outputs");
   std::vector<int64_t> counts(n);
   std::vector<TilePlan> plans(n);

@@ -237,6 +237,27 @@ int plan_for(const zmc_scan_desc* d, int64_t count, TilePlan* tp) {
     sm = ds->prop.multiProcessorCount;
     tps = ds->prop.maxThreadsPerMultiProcessor;
   }
+  // A class entry recorded by the autotuner, when the caller leaves tiles open.
+  int tl = 0, tb = 0, tg = 0;
+  if (!d->tile_lanes && !d->tile_splits && !d->tile_block) {
+    tune_ensure_loaded();
+    if (tune_find(d->precision, d->integrand_id, d->N, d->samples_per_point, &tl, &tb, &tg)) {
+      const int G = group_samples(d->N);
+      const int64_t Q = (d->samples_per_point + G - 1) / G;
+      int64_t splits = std::max<int64_t>(1, (Q + int64_t(tl) * tg - 1) / (int64_t(tl) * tg));
+      // small grids: enough ranges for ~4 waves of resident threads
+      const int64_t units = std::max<int64_t>(1, count * d->trials);
+      const int64_t want = int64_t(4) * std::max(1, sm) * std::max(256, tps);
+      if (units * splits * tl < want) {
+        const int64_t more = (want + units * tl - 1) / (units * tl);
+        splits = std::max(splits, std::min(more, std::max<int64_t>(1, Q / (int64_t(tl) * 64))));
+      }
+      tp->lanes = tl;
+      tp->block = tb;
+      tp->splits = static_cast<int>(std::min<int64_t>(splits, std::max<int64_t>(1, Q)));
+      return ZMC_OK;
+    }
+  }
   *tp = plan_tiles(d->N, d->samples_per_point, d->trials, count, sm, tps, d->tile_lanes,
                    d->tile_splits, d->tile_block);
   return ZMC_OK;

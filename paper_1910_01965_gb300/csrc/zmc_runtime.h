@@ -32,6 +32,9 @@ int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out);
 TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count, int threads_per_sm,
                     int lanes_req, int splits_req, int block_req);
 int plan_for(const zmc_scan_desc* d, int64_t count, TilePlan* tp);
+// Tuned-table access (zmc_tune.cu).  tune_find reads memory only.
+void tune_ensure_loaded();
+bool tune_find(int prec, int gid, int N, int64_t S, int* lanes, int* block, int* gpl);
 ScanLayout layout_for(const zmc_scan_desc* d, int64_t count, const TilePlan& tp);
 double box_volume(const zmc_scan_desc* d);
 void fill_scan_args(const zmc_scan_desc* d, int64_t count, const TilePlan& tp,

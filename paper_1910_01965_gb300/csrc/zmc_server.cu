@@ -537,6 +537,7 @@ int zmc_server_create(size_t mem_budget_bytes, const zmc_server_opts* opts, zmc_
       o.fail_alloc_every < 0)
     return fail(ZMC_EINVAL, "server options out of range");
   if (mem_budget_bytes < (size_t(1) << 20)) return fail(ZMC_EINVAL, "budget below 1 MiB");
+  tune_ensure_loaded();
   zmc_server* s = new (std::nothrow) zmc_server();
   if (!s) return fail(ZMC_ENOMEM, "host allocation failed");
   s->opts = o;

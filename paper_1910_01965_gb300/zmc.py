@@ -109,6 +109,12 @@ class zmc_server_stats(ctypes.Structure):
                 ("max_ms", ctypes.c_double), ("mem_in_use", ctypes.c_size_t),
                 ("mem_peak", ctypes.c_size_t)]
 
+class zmc_tune_result(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int), ("block", ctypes.c_int),
+                ("groups_per_lane", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("evals_per_s", ctypes.c_double), ("default_evals_per_s", ctypes.c_double)]
+
+
 PIPE_NAMES = ["FFMA", "IMAD", "IMAD.WIDE", "IMAD.HI", "LOP3", "SHF", "MUFU.RSQ",
               "MUFU.EX2+LG2", "DFMA", "PHILOX_CALL", "MUFU.EX2", "MUFU.COS"]
 
@@ -156,6 +162,11 @@ SIGNATURES = [
     ("zmc_server_stats_get", ctypes.c_int, [ctypes.c_void_p,
                                             ctypes.POINTER(zmc_server_stats)]),
     ("zmc_server_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("zmc_autotune", ctypes.c_int, [ctypes.POINTER(zmc_scan_desc), ctypes.c_int,
+                                    ctypes.POINTER(zmc_tune_result)]),
+    ("zmc_autotune_lookup", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int64, ctypes.POINTER(zmc_tune_result)]),
+    ("zmc_autotune_reset", ctypes.c_int, []),
 ]
 
 _lock = threading.Lock()
@@ -353,6 +364,26 @@ def zmc_server_stats_get(server: int) -> zmc_server_stats:
 
 def zmc_server_destroy(server: int):
     _check(load().zmc_server_destroy(ctypes.c_void_p(server)))
+
+
+def zmc_autotune(d: zmc_scan_desc, budget_ms: int = 500) -> zmc_tune_result:
+    r = zmc_tune_result()
+    _check(load().zmc_autotune(ctypes.byref(d), int(budget_ms), ctypes.byref(r)))
+    return r
+
+
+def zmc_autotune_lookup(precision, gid, N, samples):
+    r = zmc_tune_result()
+    rc = load().zmc_autotune_lookup(int(precision), int(gid), int(N), int(samples),
+                                    ctypes.byref(r))
+    if rc == ZMC_ENOTFOUND:
+        return None
+    _check(rc)
+    return r
+
+
+def zmc_autotune_reset():
+    _check(load().zmc_autotune_reset())
 
 
 class Server:
