@@ -419,6 +419,126 @@ def run_serving_bench(args, world, rank, local):
     return 0
 
 
+# Printed in the paper (Table 1, Sec. 3.1; one V100 + Xeon Silver 4110, times in
+# seconds, 10^4 samples per point, Python/Numba overhead included).
+TABLE1 = {  # (M, N): (delta_r, total_s)
+    (1, 1): (0.02512, 0.59343), (1, 2): (0.25034, 0.57227), (1, 3): (1.19949, 0.59330),
+    (1, 4): (6.19901, 0.60408), (2, 1): (0.03379, 0.61858), (2, 2): (0.16417, 0.59581),
+    (2, 3): (0.87280, 0.61055), (2, 4): (4.12216, 0.62169), (3, 1): (0.02927, 1.26269),
+    (3, 2): (0.15052, 1.51221), (3, 3): (0.78052, 1.78097), (3, 4): (4.05029, 2.07094),
+    (4, 1): (0.08806, 64.8745), (4, 2): (0.55222, 91.5998), (4, 3): (3.55857, 118.275),
+    (4, 4): (22.62904, 147.347)}
+# Table 2 (Sec. 3.2): 10^8 points x 10^5 samples, N = 6, 100 batches of 10^6 points;
+# GPU evaluation time per batch (s) and the three-node total (s).
+TABLE2 = {"V100_per_batch_s": 18.19497, "K40m_per_batch_s": 79.62744,
+          "K80_per_batch_s": 89.30734, "cluster_total_s": 721.20234}
+
+
+def sinsum_closed_form(xsum, N, a):
+    """Eq. 2 / Eq. 4 on [0, a]^N: (2 sin(a/2))^N sin(sum x + N a / 2)."""
+    return (2.0 * np.sin(a / 2.0)) ** N * np.sin(xsum + N * a / 2.0)
+
+
+def _grid_xsum(M):
+    v = np.arange(100.0)
+    xs = np.zeros(1)
+    for _ in range(M):
+        xs = (xs[:, None] + v[None, :]).ravel()
+    return xs
+
+
+def run_table1(args):
+    """Every (M, N) of Table 1 through zmc_scan_ex with host buffers: the scan,
+    its host<->device copies and delta r of Eq. 3 (|f| in the denominator)."""
+    import torch
+    from paper_1910_01965_gb300 import workloads as wl
+    from paper_1910_01965_gb300 import zmc
+    torch.cuda.set_device(0)
+    zmc.load()
+    rows = {}
+    total_evals, total_s = 0.0, 0.0
+    for M in (1, 2, 3, 4):
+        for N in (1, 2, 3, 4):
+            spec = wl.sinsum_table1(M, N, samples=args.table_samples)
+            vals = torch.tensor(spec.values, dtype=torch.float64).pin_memory().numpy()
+            mean = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+            err = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+            d, keep = zmc.make_desc(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                                    vals, spec.samples, spec.trials, spec.seed,
+                                    zmc.PRECISIONS[args.precision], flags=zmc.ZMC_F_TIMINGS)
+            o = zmc.zmc_scan_out()
+            o.mean, o.err = zmc._ptr(mean), zmc._ptr(err)
+            zmc.zmc_scan_ex(d, o)            # warm
+            t0 = time.perf_counter()
+            zmc.zmc_scan_ex(d, o)
+            wall = time.perf_counter() - t0
+            fth = sinsum_closed_form(_grid_xsum(M), N, 10.0)
+            dr = float(np.mean(np.abs(fth - mean) / np.abs(fth)))
+            paper_dr, paper_s = TABLE1[(M, N)]
+            rows["%d,%d" % (M, N)] = {
+                "delta_r": dr, "paper_delta_r": paper_dr, "h2d_ms": o.h2d_ms,
+                "kernel_ms": o.kernel_ms + o.finalize_ms, "d2h_ms": o.d2h_ms,
+                "total_s": wall, "paper_total_s": paper_s, "speedup_vs_paper": paper_s / wall,
+                "evals": spec.evals}
+            total_evals += spec.evals
+            total_s += wall
+    line = {"metric": METRIC, "value": total_evals / total_s, "unit": "evals/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": total_s * 1e3, "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": sum(v[1] for v in TABLE1.values()) / total_s,
+            "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": "Table 1 of the paper: sine-sum (Eq. 2) on [0,10]^N, lists "
+                                   "{0..99}^M, %d samples, all 16 (M, N)" % args.table_samples,
+                       "precision": args.precision, "api": "zmc_scan_ex, pinned host buffers",
+                       "vs_baseline": "sum of the paper's total times / ours"},
+            "table1": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_table2(args):
+    """Table 2's workload on one GPU: 10^8 points x 10^5 samples, N = 6, [0,1]^6,
+    then delta r(x1, x2) of Eq. 5 (|f| in the denominator)."""
+    import torch
+    from paper_1910_01965_gb300 import workloads as wl
+    from paper_1910_01965_gb300 import zmc
+    torch.cuda.set_device(0)
+    zmc.load()
+    spec = wl.sinsum_table2(samples=args.table_samples if args.table_samples != 10_000
+                            else 100_000)
+    vals = torch.tensor(spec.values, dtype=torch.float64).pin_memory().numpy()
+    mean = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+    err = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+    d, keep = zmc.make_desc(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, vals,
+                            spec.samples, spec.trials, spec.seed,
+                            zmc.PRECISIONS[args.precision], flags=zmc.ZMC_F_TIMINGS)
+    o = zmc.zmc_scan_out()
+    o.mean, o.err = zmc._ptr(mean), zmc._ptr(err)
+    t0 = time.perf_counter()
+    zmc.zmc_scan_ex(d, o)
+    wall = time.perf_counter() - t0
+    fth = sinsum_closed_form(_grid_xsum(4), 6, 1.0)
+    rel = (np.abs(fth - mean) / np.abs(fth)).reshape(100, 100, 10000)
+    dr12 = rel.mean(axis=2)            # Eq. 5: average over (x3, x4)
+    line = {"metric": METRIC, "value": spec.evals / wall, "unit": "evals/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": TABLE2["cluster_total_s"] / wall,
+            "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": "Table 2 of the paper: sine-sum (Eq. 4) on [0,1]^6, lists "
+                                   "{0..99}^4 (1e8 points), %d samples" % spec.samples,
+                       "precision": args.precision, "api": "zmc_scan_ex, pinned host buffers",
+                       "vs_baseline": "the paper's three-node total / ours"},
+            "table2": {"total_s": wall, "h2d_ms": o.h2d_ms,
+                       "kernel_ms": o.kernel_ms + o.finalize_ms, "d2h_ms": o.d2h_ms,
+                       "paper": TABLE2,
+                       "speedup_vs_V100_100_batches": 100 * TABLE2["V100_per_batch_s"] / wall,
+                       "delta_r_x1x2_max": float(dr12.max()),
+                       "delta_r_x1x2_median": float(np.median(dr12)),
+                       "delta_r_overall": float(rel.mean())}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------- main --
 def main():
     ap = argparse.ArgumentParser()
@@ -436,6 +556,7 @@ def main():
     ap.add_argument("--serve-window", type=float, default=1.0)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--tune-ms", type=int, default=300)
+    ap.add_argument("--table-samples", type=int, default=10_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -446,6 +567,12 @@ def main():
                               "the reference arm times the oracle on the headline workload"}))
             return 0
         return run_batch_bench(args, world, rank, local)
+    if args.workload in ("table1", "table2"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the reference arm times the oracle on the headline workload"}))
+            return 0
+        return run_table1(args) if args.workload == "table1" else run_table2(args)
     if args.workload == "serving":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":
