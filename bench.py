@@ -539,6 +539,62 @@ def run_table2(args):
     return 0
 
 
+def run_precision_stress(args):
+    """The oscillatory scan on [0,2]^6 in FP32, FP32-Kahan and FP64: throughput
+    and the worst deviation from the FP64 oracle on seeded grid points."""
+    import torch
+    from oracle import oracle
+    from paper_1910_01965_gb300 import workloads as wl
+    from paper_1910_01965_gb300 import zmc
+    torch.cuda.set_device(0)
+    zmc.load()
+    spec = wl.scan_osc_1e4()
+    pts = wl.sample_points(spec.P, args.stress_points, seed=31)
+    t0 = time.perf_counter()
+    ref = oracle.default().scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi,
+                                       spec.lengths, spec.values, spec.samples, spec.trials,
+                                       spec.seed, pts, want_sums=True)
+    oracle_s = time.perf_counter() - t0
+    vals = torch.tensor(spec.values, dtype=torch.float64, device="cuda")
+    mean = torch.empty(spec.P, dtype=torch.float64, device="cuda")
+    err = torch.empty_like(mean)
+    out = {}
+    for name in ("fp32", "fp32_kahan", "fp64"):
+        p = zmc.PRECISIONS[name]
+        o = zmc.scan_device(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, vals,
+                            spec.samples, spec.trials, spec.seed, mean, err, precision=p,
+                            flags=zmc.ZMC_F_TIMINGS)
+        if name != "fp64":
+            o = zmc.scan_device(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                                vals, spec.samples, spec.trials, spec.seed, mean, err,
+                                precision=p, flags=zmc.ZMC_F_TIMINGS)
+        got = {"mean": mean.cpu().numpy(), "err": err.cpu().numpy()}
+        out[name] = dict(accuracy(spec, pts, ref, got),
+                         evals_per_s=spec.evals / ((o.kernel_ms + o.finalize_ms) * 1e-3),
+                         kernel_ms=o.kernel_ms)
+    # One thread per (point, trial) summing all 2^20 samples (the paper's
+    # thread-per-point layout, Sec. 2): where plain FP32 sums drift.
+    for name in ("fp32", "fp32_kahan"):
+        o = zmc.scan_device(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, vals,
+                            spec.samples, spec.trials, spec.seed, mean, err,
+                            precision=zmc.PRECISIONS[name], tiles=(1, 1, 64),
+                            flags=zmc.ZMC_F_TIMINGS)
+        got = {"mean": mean.cpu().numpy(), "err": err.cpu().numpy()}
+        out[name + "_one_thread_per_unit"] = dict(
+            accuracy(spec, pts, ref, got),
+            evals_per_s=spec.evals / ((o.kernel_ms + o.finalize_ms) * 1e-3))
+    line = {"metric": METRIC, "value": out["fp32_kahan"]["evals_per_s"], "unit": "evals/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": out["fp32_kahan"]["kernel_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(spec.describe(), compared_points=int(pts.size),
+                           oracle_seconds=oracle_s),
+            "precisions": out,
+            "fp32_kahan_over_fp64": out["fp32_kahan"]["evals_per_s"] / out["fp64"]["evals_per_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------- main --
 def main():
     ap = argparse.ArgumentParser()
@@ -557,6 +613,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--tune-ms", type=int, default=300)
     ap.add_argument("--table-samples", type=int, default=10_000)
+    ap.add_argument("--stress-points", type=int, default=48)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -567,6 +624,12 @@ def main():
                               "the reference arm times the oracle on the headline workload"}))
             return 0
         return run_batch_bench(args, world, rank, local)
+    if args.workload == "precision_stress":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the reference arm times the oracle on the headline workload"}))
+            return 0
+        return run_precision_stress(args)
     if args.workload in ("table1", "table2"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":

@@ -10,6 +10,12 @@
 // keys into registers, and runs the same per-lane sampling and reduction code
 // as the single-scan kernel, writing each unit-split's FP64 partial sums into
 // that scan's slice of the batch's partial buffer.
+// Two sample groups in flight per lane keep every batched body within 64
+// registers; the order of the compensated additions is the same as with the
+// single-scan kernel's four, so results stay bit-identical to solo runs.
+#ifndef ZMC_PAIR_GROUPS
+#define ZMC_PAIR_GROUPS 2
+#endif
 #include "zmc_scan_kernel.cuh"
 
 #ifndef ZMC_INST_PREC

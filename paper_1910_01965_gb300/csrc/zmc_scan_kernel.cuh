@@ -30,13 +30,16 @@ enum { kPrecFP64 = ZMC_FP64, kPrecFP32 = ZMC_FP32, kPrecFP32K = ZMC_FP32_KAHAN }
 #define ZMC_LB_THREADS 512   // __launch_bounds__ maximum block size
 #endif
 #ifndef ZMC_LB_MIN_BLOCKS
-#define ZMC_LB_MIN_BLOCKS 2  // __launch_bounds__ minimum resident blocks
+#define ZMC_LB_MIN_BLOCKS 1  // __launch_bounds__ minimum resident blocks
 #endif
 #ifndef ZMC_UNROLL_SMALL
 #define ZMC_UNROLL_SMALL 2   // sample groups in flight per lane when C <= 2
 #endif
 #ifndef ZMC_KAHAN_PAIRS
 #define ZMC_KAHAN_PAIRS 1    // 1: compensated sums take pairs of samples
+#endif
+#ifndef ZMC_PAIR_GROUPS
+#define ZMC_PAIR_GROUPS 4    // groups in flight per lane when G == 1 (2 or 4)
 #endif
 
 template <int PREC>
@@ -214,7 +217,7 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
   for (int c = 0; c < C; ++c) sp[c].init(q * C + c, step * C);
   if constexpr (ZMC_KAHAN_PAIRS && (G % 2 == 0 || kUnroll % 2 == 0)) {
     // Samples enter the sums two at a time.
-    constexpr int U = (G % 2 == 0) ? 1 : 2;
+    constexpr int U = (G % 2 == 0) ? 1 : ZMC_PAIR_GROUPS;
     for (; q + (U - 1) * step < q_end; q += U * step) {
       uint32_t r[U][4 * C];
 #pragma unroll
@@ -228,6 +231,24 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
 #pragma unroll
         for (int g = 0; g < G; g += 2) acc.add2(f.eval(&r[0][g * N]), f.eval(&r[0][(g + 1) * N]));
       } else {
+#pragma unroll
+        for (int u = 0; u < U; u += 2)
+#pragma unroll
+          for (int g = 0; g < G; ++g) acc.add2(f.eval(&r[u][g * N]), f.eval(&r[u + 1][g * N]));
+      }
+    }
+    // Fewer than U groups left: pairs, then a single group, so that the order
+    // of the compensated additions is the same for any U.
+    if constexpr (U > 2) {
+      for (; q + step < q_end; q += 2 * step) {
+        uint32_t r[2][4 * C];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[u][4 * c]);
+            sp[c].advance();
+          }
 #pragma unroll
         for (int g = 0; g < G; ++g) acc.add2(f.eval(&r[0][g * N]), f.eval(&r[1][g * N]));
       }
