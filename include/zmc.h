@@ -80,7 +80,9 @@ enum { ZMC_MEM_HOST = 0, ZMC_MEM_DEVICE = 1 };
 enum {
   ZMC_F_TIMINGS = 1,  /* record CUDA-event timings into zmc_scan_out; the
                          call then waits for its work before returning   */
-  ZMC_F_SYNC = 2      /* wait for the enqueued work before returning      */
+  ZMC_F_SYNC = 2,     /* wait for the enqueued work before returning      */
+  ZMC_F_PLAN_ONLY = 4 /* validate and plan: fill the tile fields of the
+                         output struct and return without computing      */
 };
 
 /*

@@ -32,6 +32,10 @@ constexpr double kOscQuad = 0.1;
 // sqrt(log2(e) / (2 sigma^2)) for sigma = 0.3: scales (y - x) so that
 // exp(-(y-x)^2 / (2 sigma^2)) = 2^-(d^2).
 constexpr double kGaussScale = 2.83107266762673;  // to double precision
+// 1 / (2 sigma^2) for sigma = 0.3: the FP64 Gaussian multiplies instead of
+// dividing (FP64 division is an iteration on GB300's narrow FP64 pipe); the
+// two differ by at most one unit in the last place of the exponent.
+constexpr double kGaussInvTwoSigma2 = 5.555555555555555;
 
 __device__ __forceinline__ float unit_f12(uint32_t r) {
   // 1 + (r>>9) 2^-23: one funnel shift of (0x7f : r) right by 9 places the
@@ -98,7 +102,7 @@ struct Gauss64 {
       const double d = fma(w[k], unit_u64(r[k]), a[k]) - x[k];
       q += d * d;
     }
-    return exp(-q / (2.0 * kGaussSigma * kGaussSigma));
+    return exp(-q * kGaussInvTwoSigma2);
   }
 };
 

@@ -368,14 +368,16 @@ int scan_ex(const zmc_scan_desc* d, zmc_scan_out* o) {
   int rc = validate(d, &P, &count);
   if (rc != ZMC_OK) return rc;
   if (!o) return fail(ZMC_EINVAL, "output struct is NULL");
-  if (count > 0 && (!o->mean || !o->err)) return fail(ZMC_EINVAL, "mean/err output is NULL");
+  const bool plan_only = (d->flags & ZMC_F_PLAN_ONLY) != 0;
+  if (count > 0 && !plan_only && (!o->mean || !o->err))
+    return fail(ZMC_EINVAL, "mean/err output is NULL");
 
   DeviceState* ds = nullptr;
   rc = device_state(&ds);
   if (rc != ZMC_OK) return rc;
   cudaStream_t stream = static_cast<cudaStream_t>(d->stream);  // NULL: default stream
 
-  if (d->mem == ZMC_MEM_DEVICE) {
+  if (d->mem == ZMC_MEM_DEVICE && !plan_only) {
     const void* ptrs[6] = {d->list_vals, o->mean, o->err, o->errw, o->s1, o->s2};
     for (int i = 0; i < 6; ++i)
       if (ptrs[i] && !is_device_ptr(ptrs[i]))
@@ -392,7 +394,7 @@ int scan_ex(const zmc_scan_desc* d, zmc_scan_out* o) {
   o->tile_block = tp.block;
   o->launches = 0;
   o->h2d_ms = o->kernel_ms = o->finalize_ms = o->d2h_ms = o->total_ms = 0.0f;
-  if (count == 0) return ZMC_OK;
+  if (count == 0 || (d->flags & ZMC_F_PLAN_ONLY)) return ZMC_OK;
 
   // Scratch: the caller's workspace or the stream-ordered pool.
   char* ws = static_cast<char*>(d->workspace);

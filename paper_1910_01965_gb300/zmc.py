@@ -23,7 +23,7 @@ ZMC_FP64, ZMC_FP32, ZMC_FP32_KAHAN = range(3)
 ZMC_G_CONST, ZMC_G_COSPROD, ZMC_G_GAUSS03, ZMC_G_POLY, ZMC_G_OSC01, \
     ZMC_G_SINSUM, ZMC_G_COUNT = range(7)
 ZMC_MEM_HOST, ZMC_MEM_DEVICE = 0, 1
-ZMC_F_TIMINGS, ZMC_F_SYNC = 1, 2
+ZMC_F_TIMINGS, ZMC_F_SYNC, ZMC_F_PLAN_ONLY = 1, 2, 4
 ZMC_MAX_N, ZMC_MAX_M = 8, 16
 
 STATUS_NAMES = {0: "ZMC_OK", 1: "ZMC_EINVAL", 2: "ZMC_ENOMEM", 3: "ZMC_ECUDA",
