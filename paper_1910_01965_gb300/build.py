@@ -114,7 +114,7 @@ def build(force: bool = False, jobs: int = 0, verbose: bool = False,
         list(ex.map(compile_one, units))
     objs = [os.path.join(BUILD_, u[0]) for u in units]
     tmp = lib + ".tmp.%d" % os.getpid()
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-ldl",
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

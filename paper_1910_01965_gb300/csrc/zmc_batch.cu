@@ -163,6 +163,8 @@ int batch_create(const zmc_scan_desc* d, zmc_scan_out* o, int n, int flags, zmc_
     if (rc != ZMC_OK) return fail(rc, "scan %d: %s", i, last_error());
     if (d[i].mem != ZMC_MEM_DEVICE)
       return fail(ZMC_EINVAL, "scan %d: a batch object needs ZMC_MEM_DEVICE", i);
+    if (is_user_integrand(d[i].integrand_id))
+      return fail(ZMC_EINVAL, "scan %d: batches take the compiled-in integrands only", i);
     if (d[i].tile_block != 0 && d[i].tile_block != kBatchBlock)
       return fail(ZMC_EINVAL, "scan %d: batches run %d-thread blocks", i, kBatchBlock);
     if (counts[i] > 0 && (!o[i].mean || !o[i].err))

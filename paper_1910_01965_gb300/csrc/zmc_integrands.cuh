@@ -15,6 +15,8 @@
 //    integrand's own arithmetic.  cos/sin use the SFU (MUFU) approximations,
 //    exp uses ex2.approx.
 //
+// kFixedM > 0 marks a functor compiled for one number of parameters M (the
+// run-time-compiled user integrands); it receives parameter i by set_param.
 // `set(i, x_i, a_i, b_i)` receives parameter i and box side i (kPerDim: the
 // integrand pairs x_k with y_k, M == N); `add(x_i)` receives parameters of the
 // any-M integrands; `finish(lo, hi)` runs once after the parameters.  FP32
@@ -64,6 +66,7 @@ struct Const64 {
   static constexpr bool kPerDim = false;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = false;
+  static constexpr int kFixedM = 0;
   __device__ void add(double) {}
   __device__ void finish(const double*, const double*) {}
   __device__ double eval(const uint32_t*) const { return 1.0; }
@@ -74,6 +77,7 @@ struct CosProd64 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   double x[N], w[N], a[N];
   __device__ void set(int i, double xi, double ai, double bi) {
     x[i] = xi; a[i] = ai; w[i] = bi - ai;
@@ -91,6 +95,7 @@ struct Gauss64 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   double x[N], w[N], a[N];
   __device__ void set(int i, double xi, double ai, double bi) {
     x[i] = xi; a[i] = ai; w[i] = bi - ai;
@@ -111,6 +116,7 @@ struct Poly64 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   double x[N], w[N], a[N];
   __device__ void set(int i, double xi, double ai, double bi) {
     x[i] = xi; a[i] = ai; w[i] = bi - ai;
@@ -131,6 +137,7 @@ struct Osc64 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   double x[N], w[N], a[N];
   __device__ void set(int i, double xi, double ai, double bi) {
     x[i] = xi; a[i] = ai; w[i] = bi - ai;
@@ -152,6 +159,7 @@ struct SinSum64 {
   static constexpr bool kPerDim = false;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   double xsum, w[N], a[N];
   __device__ void add(double xi) { xsum += xi; }
   __device__ void finish(const double* lo, const double* hi) {
@@ -178,6 +186,7 @@ struct Const32 {
   static constexpr bool kPerDim = false;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = false;
+  static constexpr int kFixedM = 0;
   __device__ void add(double) {}
   __device__ void finish(const double*, const double*) {}
   __device__ float eval(const uint32_t*) const { return 1.0f; }
@@ -189,6 +198,7 @@ struct CosProd32 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   float B[N], C[N];
   static __device__ float2 value(int, double x, double a, double b) {
     const double w = b - a;
@@ -212,6 +222,7 @@ struct Gauss32 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   float B[N], C[N];
   static __device__ float2 value(int, double x, double a, double b) {
     const double w = b - a;
@@ -239,6 +250,7 @@ struct Poly32 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   float W[N], A[N], X[N];
   static __device__ float2 value(int, double x, double, double) {
     return make_float2(static_cast<float>(x), 0.f);
@@ -267,6 +279,7 @@ struct Osc32 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   float W[N], A[N], X[N];
   static __device__ float2 value(int, double x, double, double) {
     return make_float2(static_cast<float>(x), 0.f);
@@ -295,6 +308,7 @@ struct SinSum32 {
   static constexpr bool kPerDim = false;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kFixedM = 0;
   double xsum;
   float W[N], C0;
   __device__ void add(double xi) { xsum += xi; }

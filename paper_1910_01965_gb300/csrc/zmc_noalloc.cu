@@ -75,6 +75,8 @@ static int scan_noalloc(const zmc_scan_desc* d, zmc_scan_out* o) {
   if (!o) return fail(ZMC_EINVAL, "output struct is NULL");
   if (d->mem != ZMC_MEM_DEVICE)
     return fail(ZMC_EINVAL, "zmc_scan_noalloc needs ZMC_MEM_DEVICE lists and outputs");
+  if (is_user_integrand(d->integrand_id))  // loading their code would allocate
+    return fail(ZMC_EINVAL, "zmc_scan_noalloc takes the compiled-in integrands only");
   if (d->workspace)
     return fail(ZMC_EINVAL, "zmc_scan_noalloc takes no workspace (its scratch is built in)");
   if (d->flags & ZMC_F_TIMINGS)

@@ -105,13 +105,19 @@ static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out) {
   if (!d) return fail(ZMC_EINVAL, "descriptor is NULL");
-  if (d->integrand_id < 0 || d->integrand_id >= ZMC_G_COUNT)
+  const bool user = is_user_integrand(d->integrand_id);
+  if (!user && (d->integrand_id < 0 || d->integrand_id >= ZMC_G_COUNT))
     return fail(ZMC_ENOTFOUND, "unknown integrand id %d", d->integrand_id);
   if (d->N < 1 || d->N > ZMC_MAX_N)
     return fail(ZMC_EINVAL, "N = %d outside [1, %d]", d->N, ZMC_MAX_N);
   if (d->M < 1 || d->M > ZMC_MAX_M)
     return fail(ZMC_EINVAL, "M = %d outside [1, %d]", d->M, ZMC_MAX_M);
-  const bool m_is_n = d->integrand_id != ZMC_G_CONST && d->integrand_id != ZMC_G_SINSUM;
+  if (user) {
+    const int ur = user_validate(d);
+    if (ur != ZMC_OK) return ur;
+  }
+  const bool m_is_n = !user && d->integrand_id != ZMC_G_CONST &&
+                      d->integrand_id != ZMC_G_SINSUM;
   if (m_is_n && d->M != d->N)
     return fail(ZMC_EINVAL, "integrand %d needs M == N (got M = %d, N = %d)",
                 d->integrand_id, d->M, d->N);
@@ -317,6 +323,13 @@ void fill_scan_args(const zmc_scan_desc* d, int64_t count, const TilePlan& tp,
 int launch_scan_args(const zmc_scan_desc* d, const ScanArgs& a, const TilePlan& tp,
                      cudaStream_t stream) {
   if (a.n_us == 0) return ZMC_OK;
+  if (is_user_integrand(d->integrand_id)) {
+    const int64_t per_block = tp.block / tp.lanes;
+    const int64_t grid = (a.n_us + per_block - 1) / per_block;
+    if (grid > 0x7fffffffLL) return fail(ZMC_EINVAL, "launch grid too large (%lld)", (long long)grid);
+    const size_t smem = a.stage_smem ? static_cast<size_t>(a.nvals) * sizeof(double) : 0;
+    return user_launch(d, a, tp.block, grid, smem, stream);
+  }
   ScanLaunchFn fn = scan_launcher(d->precision, d->integrand_id, d->N);
   if (!fn) return fail(ZMC_ENOTFOUND, "no kernel for integrand %d, N %d", d->integrand_id, d->N);
   const int64_t per_block = tp.block / tp.lanes;
@@ -534,6 +547,7 @@ int zmc_integrand_info_get(int id, zmc_integrand_info* info) {
   static const char* names[ZMC_G_COUNT] = {"const", "cosprod", "gauss03",
                                            "poly", "osc01", "sinsum"};
   if (!info) return fail(ZMC_EINVAL, "info is NULL");
+  if (is_user_integrand(id)) return user_info(id, info);
   if (id < 0 || id >= ZMC_G_COUNT) return fail(ZMC_ENOTFOUND, "unknown integrand id %d", id);
   std::memset(info, 0, sizeof(*info));
   info->id = id;

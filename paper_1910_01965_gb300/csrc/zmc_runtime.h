@@ -32,6 +32,12 @@ int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out);
 TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count, int threads_per_sm,
                     int lanes_req, int splits_req, int block_req);
 int plan_for(const zmc_scan_desc* d, int64_t count, TilePlan* tp);
+// User integrands compiled at run time (zmc_user.cu).
+bool is_user_integrand(int id);
+int user_validate(const zmc_scan_desc* d);
+int user_info(int id, zmc_integrand_info* info);
+int user_launch(const zmc_scan_desc* d, const ScanArgs& a, int block, int64_t grid, size_t smem,
+                cudaStream_t stream);
 // Tuned-table access (zmc_tune.cu).  tune_find reads memory only.
 void tune_ensure_loaded();
 bool tune_find(int prec, int gid, int N, int64_t S, int* lanes, int* block, int* gpl);

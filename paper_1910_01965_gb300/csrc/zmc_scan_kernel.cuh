@@ -152,6 +152,15 @@ __device__ __forceinline__ void load_params(const ScanArgs& a, const void* table
                              : F::value(i, a.vals[idx], a.lo[i], a.hi[i]);
       f.load(i, v, &dimc[3 * i]);
     }
+  } else if constexpr (F::kFixedM > 0) {
+    // one compiled M: the parameters land in registers
+    const double* vals = table ? static_cast<const double*>(table) : a.vals;
+#pragma unroll
+    for (int i = F::kFixedM - 1; i >= 0; --i) {
+      const int64_t d = next_digit(a, p, a.len[i]);
+      f.set_param(i, vals[a.off[i] + d]);
+    }
+    f.finish(a.lo, a.hi);
   } else if constexpr (F::kPerDim) {
     // M == N: parameter i pairs with dimension i.
     const double* vals = table ? static_cast<const double*>(table) : a.vals;
@@ -385,6 +394,7 @@ scan_kernel(const __grid_constant__ ScanArgs a) {
   }
 }
 
+#ifndef __CUDACC_RTC__
 template <int N, class F, int PREC>
 int launch_scan(const ScanArgs& a, int block, int64_t grid, size_t smem, void* stream) {
   if (smem > 48 * 1024) {
@@ -397,5 +407,6 @@ int launch_scan(const ScanArgs& a, int block, int64_t grid, size_t smem, void* s
                             static_cast<cudaStream_t>(stream)>>>(a);
   return static_cast<int>(cudaGetLastError());
 }
+#endif  // __CUDACC_RTC__
 
 }  // namespace zmc

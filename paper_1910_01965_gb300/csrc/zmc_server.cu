@@ -576,6 +576,8 @@ int zmc_submit(zmc_server* s, const zmc_scan_desc* d, zmc_scan_out* o, uint64_t*
   int rc = validate(d, &P, &count);
   if (rc != ZMC_OK) return rc;
   if (d->mem != ZMC_MEM_HOST) return fail(ZMC_EINVAL, "served requests use ZMC_MEM_HOST");
+  if (is_user_integrand(d->integrand_id))
+    return fail(ZMC_EINVAL, "the server takes the compiled-in integrands only");
   if (d->tile_block != 0 && d->tile_block != kServeBlock)
     return fail(ZMC_EINVAL, "served requests run %d-thread blocks", kServeBlock);
   if (count > 0 && (!o->mean || !o->err)) return fail(ZMC_EINVAL, "mean/err output is NULL");

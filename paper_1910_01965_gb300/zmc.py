@@ -167,6 +167,8 @@ SIGNATURES = [
     ("zmc_autotune_lookup", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int64, ctypes.POINTER(zmc_tune_result)]),
     ("zmc_autotune_reset", ctypes.c_int, []),
+    ("zmc_integrand_register", ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int,
+                                              ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
 ]
 
 _lock = threading.Lock()
@@ -384,6 +386,18 @@ def zmc_autotune_lookup(precision, gid, N, samples):
 
 def zmc_autotune_reset():
     _check(load().zmc_autotune_reset())
+
+
+ZMC_G_USER_BASE = 1000
+
+
+def zmc_integrand_register(name: str, source: str, n_min: int = 1, n_max: int = ZMC_MAX_N):
+    """Compile a user integrand (CUDA C source defining zmc_user_g32 and/or
+    zmc_user_g64) with NVRTC; returns its integrand id."""
+    i = ctypes.c_int()
+    _check(load().zmc_integrand_register(name.encode(), source.encode(), int(n_min),
+                                         int(n_max), ctypes.byref(i)))
+    return int(i.value)
 
 
 class Server:
