@@ -369,6 +369,42 @@ def run_batch_bench(args, world, rank, local):
     b.record(stream)
     torch.cuda.synchronize()
     seq_ms = a.elapsed_time(b)
+    # Many small scans (the serving mix's typical request): separate launches
+    # are overhead-bound there, one persistent launch is not.
+    small = [s for s in wl.batch_uneven_256(count=2048, seed=7)]
+    for s_ in small:
+        s_.samples = int(min(s_.samples, 1 << 11))
+        s_.lists = [v[:min(len(v), 8)] for v in s_.lists]
+    sd, so, sk = [], [], []
+    for sp in small:
+        vals = torch.tensor(sp.values, dtype=torch.float64, device="cuda")
+        d, k = zmc.make_desc(sp.integrand_id, sp.N, sp.lo, sp.hi, sp.lengths, vals, sp.samples,
+                             sp.trials, sp.seed, prec, mem=zmc.ZMC_MEM_DEVICE)
+        d.stream = stream.cuda_stream
+        m = torch.empty(sp.P, dtype=torch.float64, device="cuda")
+        e = torch.empty_like(m)
+        o = zmc.zmc_scan_out()
+        o.mean, o.err = zmc._ptr(m), zmc._ptr(e)
+        sd.append(d)
+        so.append(o)
+        sk.append((k, vals, m, e))
+    small_evals = float(sum(sp.evals for sp in small))
+    hs = zmc.zmc_batch_create(sd, so, zmc.ZMC_BATCH_GRAPH)
+    zmc.zmc_batch_run(hs, stream.cuda_stream)
+    a.record(stream)
+    zmc.zmc_batch_run(hs, stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    small_batch_ms = a.elapsed_time(b)
+    zmc.zmc_batch_destroy(hs)
+    for d, o in zip(sd, so):
+        zmc.zmc_scan_ex(d, o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d, o in zip(sd, so):
+        zmc.zmc_scan_ex(d, o)
+    torch.cuda.synchronize()
+    small_sep_ms = (time.perf_counter() - t0) * 1e3
     info_d = zmc.zmc_device_info_get()
     peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
     f_max = json.load(open(peaks)).get("sm_max_mhz") if os.path.exists(peaks) else None
@@ -390,6 +426,11 @@ def run_batch_bench(args, world, rank, local):
                          "kernel": "batch_kernel (persistent)"},
             "separate_launches": {"ms": seq_ms, "evals_per_s": evals / (seq_ms * 1e-3),
                                   "launches": 2 * len(specs), "tiles": "autotuned"},
+            "small_scans_2048": {"scans": len(small), "evaluations": small_evals,
+                                 "batch_ms": small_batch_ms,
+                                 "separate_launches_ms": small_sep_ms,
+                                 "batch_evals_per_s": small_evals / (small_batch_ms * 1e-3),
+                                 "separate_evals_per_s": small_evals / (small_sep_ms * 1e-3)},
             "autotune": {"classes": tuned, "tune_s": tune_s,
                          "untuned_batch_ms": untuned_ms,
                          "untuned_evals_per_s": evals / (untuned_ms * 1e-3)},
