@@ -5,8 +5,8 @@
 // u = (2 (r >> 9) + 1) 2^-24, y = a + (b - a) u.
 //
 // Two families:
-//  * FP64 functors (suffix 64) form y exactly as written above in FP64 and
-//    evaluate g in FP64.
+//  * FP64 functors (suffix 64) evaluate y and g in FP64, with the affine
+//    steps folded into per-unit constants as below.
 //  * FP32 functors (suffix 32) build the float f = 1 + (r >> 9) 2^-23 from the
 //    word's bits, so u = f - (1 - 2^-24) and y = (b - a) f + A with
 //    A = a - (b - a)(1 - 2^-24).  Everything affine in y that depends only on
@@ -61,6 +61,17 @@ __device__ __forceinline__ float ex2_approx(float v) {
 }
 
 // ------------------------------------------------------------------ FP64 --
+// FP64 functors fold the affine steps in y into per-unit constants the same way
+// the FP32 ones do: f = 1 + (r >> 9) 2^-23 exactly (built from bits), y =
+// (b - a) f + A with A = a - (b - a)(1 - 2^-24), so each dimension costs one
+// DFMA before the integrand's own arithmetic.  The result differs from
+// forming u first by at most a unit in the last place of each coordinate.
+
+__device__ __forceinline__ double unit_f64(uint32_t r) {
+  return __longlong_as_double(static_cast<long long>(
+      0x3FF0000000000000ull | (static_cast<uint64_t>(r >> 9) << 29)));
+}
+
 template <int N>
 struct Const64 {
   static constexpr bool kPerDim = false;
@@ -72,40 +83,47 @@ struct Const64 {
   __device__ double eval(const uint32_t*) const { return 1.0; }
 };
 
+// cos(x y) = cos(B f + C), B = x (b - a), C = x A.
 template <int N>
 struct CosProd64 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
-  double x[N], w[N], a[N];
+  double B[N], C[N];
   __device__ void set(int i, double xi, double ai, double bi) {
-    x[i] = xi; a[i] = ai; w[i] = bi - ai;
+    const double w = bi - ai;
+    B[i] = xi * w;
+    C[i] = xi * (ai - w * kOneMinusHalfUlp);
   }
   __device__ double eval(const uint32_t* r) const {
-    double g = cos(x[0] * fma(w[0], unit_u64(r[0]), a[0]));
+    double g = cos(fma(B[0], unit_f64(r[0]), C[0]));
 #pragma unroll
-    for (int k = 1; k < N; ++k) g *= cos(x[k] * fma(w[k], unit_u64(r[k]), a[k]));
+    for (int k = 1; k < N; ++k) g *= cos(fma(B[k], unit_f64(r[k]), C[k]));
     return g;
   }
 };
 
+// y - x = W f + C, C = A - x.
 template <int N>
 struct Gauss64 {
   static constexpr bool kPerDim = true;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
-  double x[N], w[N], a[N];
+  double W[N], C[N];
   __device__ void set(int i, double xi, double ai, double bi) {
-    x[i] = xi; a[i] = ai; w[i] = bi - ai;
+    const double w = bi - ai;
+    W[i] = w;
+    C[i] = (ai - w * kOneMinusHalfUlp) - xi;
   }
   __device__ double eval(const uint32_t* r) const {
-    double q = 0.0;
+    double d = fma(W[0], unit_f64(r[0]), C[0]);
+    double q = d * d;
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const double d = fma(w[k], unit_u64(r[k]), a[k]) - x[k];
-      q += d * d;
+    for (int k = 1; k < N; ++k) {
+      d = fma(W[k], unit_f64(r[k]), C[k]);
+      q = fma(d, d, q);
     }
     return exp(-q * kGaussInvTwoSigma2);
   }
@@ -117,16 +135,20 @@ struct Poly64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
-  double x[N], w[N], a[N];
+  double W[N], A[N], X[N];
   __device__ void set(int i, double xi, double ai, double bi) {
-    x[i] = xi; a[i] = ai; w[i] = bi - ai;
+    const double w = bi - ai;
+    W[i] = w;
+    A[i] = ai - w * kOneMinusHalfUlp;
+    X[i] = xi;
   }
   __device__ double eval(const uint32_t* r) const {
-    double g = 1.0;
+    double y = fma(W[0], unit_f64(r[0]), A[0]);
+    double g = fma(X[0] * y, y, 1.0);
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const double y = fma(w[k], unit_u64(r[k]), a[k]);
-      g *= 1.0 + x[k] * y * y;
+    for (int k = 1; k < N; ++k) {
+      y = fma(W[k], unit_f64(r[k]), A[k]);
+      g *= fma(X[k] * y, y, 1.0);
     }
     return g;
   }
@@ -138,39 +160,49 @@ struct Osc64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
-  double x[N], w[N], a[N];
+  double W[N], A[N], X[N];
   __device__ void set(int i, double xi, double ai, double bi) {
-    x[i] = xi; a[i] = ai; w[i] = bi - ai;
+    const double w = bi - ai;
+    W[i] = w;
+    A[i] = ai - w * kOneMinusHalfUlp;
+    X[i] = xi;
   }
   __device__ double eval(const uint32_t* r) const {
     double lin = 0.0, quad = 0.0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      const double y = fma(w[k], unit_u64(r[k]), a[k]);
-      lin += x[k] * y;
-      quad += y * y;
+      const double y = fma(W[k], unit_f64(r[k]), A[k]);
+      lin = fma(X[k], y, lin);
+      quad = fma(y, y, quad);
     }
-    return cos(lin + kOscQuad * quad);
+    return cos(fma(kOscQuad, quad, lin));
   }
 };
 
+// sin(sum_k W_k f_k + C0), C0 = sum_k A_k + sum_l x_l.
 template <int N>
 struct SinSum64 {
   static constexpr bool kPerDim = false;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
-  double xsum, w[N], a[N];
+  double xsum, W[N], C0;
   __device__ void add(double xi) { xsum += xi; }
   __device__ void finish(const double* lo, const double* hi) {
+    double c = xsum;
 #pragma unroll
-    for (int k = 0; k < N; ++k) { a[k] = lo[k]; w[k] = hi[k] - lo[k]; }
+    for (int k = 0; k < N; ++k) {
+      const double w = hi[k] - lo[k];
+      W[k] = w;
+      c += lo[k] - w * kOneMinusHalfUlp;
+    }
+    C0 = c;
   }
   __device__ double eval(const uint32_t* r) const {
-    double s = 0.0;
+    double s = C0;
 #pragma unroll
-    for (int k = 0; k < N; ++k) s += fma(w[k], unit_u64(r[k]), a[k]);
-    return sin(s + xsum);
+    for (int k = 0; k < N; ++k) s = fma(W[k], unit_f64(r[k]), s);
+    return sin(s);
   }
 };
 

@@ -140,6 +140,12 @@ static void finish_request(zmc_server* s, const std::shared_ptr<Request>& r, int
   } else {
     s->failed++;
   }
+  // The input copies are not needed any more; a finished ticket keeps only
+  // its status (so a long-running server does not accumulate the lists).
+  std::vector<double>().swap(r->vals);
+  std::vector<double>().swap(r->lo);
+  std::vector<double>().swap(r->hi);
+  std::vector<int64_t>().swap(r->len);
   s->cv_done.notify_all();
 }
 
