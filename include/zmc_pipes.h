@@ -35,7 +35,13 @@ typedef enum {
   ZMC_PIPE_PHILOX = 9,     /* one Philox4x32-10 call of the sampling kernels */
   ZMC_PIPE_MUFU_EX2 = 10,  /* ex2.approx.ftz.f32 of a negated input (SFU)  */
   ZMC_PIPE_MUFU_COS = 11,  /* cos.approx.ftz.f32 (SFU, plus its scaling)   */
-  ZMC_PIPE_COUNT = 12
+  ZMC_PIPE_FFMA2 = 12,     /* fma.rn.f32x2 (two FP32 FMAs per instruction) */
+  /* Mixed probes, counted in wide multiplies: each step is one mad.wide.u32
+   * plus two FP32 FMAs, as two scalar instructions or one packed one, to show
+   * whether the FP32 work takes issue cycles from the wide multiplies. */
+  ZMC_PIPE_WIDE_FFMA = 13,
+  ZMC_PIPE_WIDE_FFMA2 = 14,
+  ZMC_PIPE_COUNT = 15
 } zmc_pipe;
 
 typedef struct zmc_pipe_result {

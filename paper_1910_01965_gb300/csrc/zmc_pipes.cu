@@ -15,6 +15,7 @@ constexpr int kChains = 8;
 template <int PIPE>
 __device__ __forceinline__ void pipe_step(uint32_t (&u)[kChains], float (&f)[kChains],
                                           double (&d)[kChains], uint64_t (&w)[kChains],
+                                          uint64_t (&v)[kChains], uint64_t vab,
                                           uint32_t c1, uint32_t c2, float fa, float fb,
                                           double da, double db, const PhiloxUnit& pu,
                                           const uint32_t* rk0, const uint32_t* rk1) {
@@ -45,6 +46,17 @@ __device__ __forceinline__ void pipe_step(uint32_t (&u)[kChains], float (&f)[kCh
       asm volatile("lg2.approx.ftz.f32 %0, %0;" : "+f"(f[k]));
     } else if constexpr (PIPE == ZMC_PIPE_DFMA) {
       asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(d[k]) : "d"(da), "d"(db));
+    } else if constexpr (PIPE == ZMC_PIPE_FFMA2) {
+      asm volatile("fma.rn.f32x2 %0, %0, %1, %1;" : "+l"(v[k]) : "l"(vab));
+    } else if constexpr (PIPE == ZMC_PIPE_WIDE_FFMA) {
+      asm volatile("{ .reg .u32 t; cvt.u32.u64 t, %0; mad.wide.u32 %0, t, %1, %0; }"
+                   : "+l"(w[k]) : "r"(c1));
+      asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(f[k]) : "f"(fa), "f"(fb));
+      asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(f[k]) : "f"(fa), "f"(fb));
+    } else if constexpr (PIPE == ZMC_PIPE_WIDE_FFMA2) {
+      asm volatile("{ .reg .u32 t; cvt.u32.u64 t, %0; mad.wide.u32 %0, t, %1, %0; }"
+                   : "+l"(w[k]) : "r"(c1));
+      asm volatile("fma.rn.f32x2 %0, %0, %1, %1;" : "+l"(v[k]) : "l"(vab));
     } else if constexpr (PIPE == ZMC_PIPE_PHILOX) {
       uint32_t r[4];
       philox_call(pu, rk0, rk1, u[k], r);
@@ -63,7 +75,7 @@ pipe_kernel(int iters, uint32_t seed, unsigned long long* cycles, uint32_t* sink
   uint32_t u[kChains];
   float f[kChains];
   double d[kChains];
-  uint64_t w[kChains];
+  uint64_t w[kChains], v[kChains];
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
   for (int k = 0; k < kChains; ++k) {
@@ -71,6 +83,7 @@ pipe_kernel(int iters, uint32_t seed, unsigned long long* cycles, uint32_t* sink
     f[k] = 1.0f + 1e-3f * k + 1e-7f * (tid & 1023);
     d[k] = 1.0 + 1e-3 * k;
     w[k] = u[k];
+    v[k] = (static_cast<uint64_t>(__float_as_uint(f[k] + 0.5f)) << 32) | __float_as_uint(f[k]);
   }
   uint32_t rk0[10], rk1[10];
 #pragma unroll
@@ -82,10 +95,12 @@ pipe_kernel(int iters, uint32_t seed, unsigned long long* cycles, uint32_t* sink
   const uint32_t c1 = 0x9E3779B9u ^ seed, c2 = 0x7f4a7c15u;
   const float fa = 0.99993f, fb = 7e-5f;
   const double da = 0.99993, db = 7e-5;
+  // (0.99993, 0.99993) as a packed pair: v = v * 0.99993 + 0.99993 stays bounded
+  const uint64_t vab = (static_cast<uint64_t>(__float_as_uint(fa)) << 32) | __float_as_uint(fa);
   __syncthreads();
   const long long t0 = clock64();
   for (int i = 0; i < iters; ++i)
-    pipe_step<PIPE>(u, f, d, w, c1, c2, fa, fb, da, db, pu, rk0, rk1);
+    pipe_step<PIPE>(u, f, d, w, v, vab, c1, c2, fa, fb, da, db, pu, rk0, rk1);
   __syncthreads();
   const long long t1 = clock64();
   uint32_t acc = 0;
@@ -99,6 +114,13 @@ pipe_kernel(int iters, uint32_t seed, unsigned long long* cycles, uint32_t* sink
       acc ^= static_cast<uint32_t>(__double_as_longlong(d[k]));
     else if constexpr (PIPE == ZMC_PIPE_IMAD_WIDE)
       acc ^= static_cast<uint32_t>(w[k]) ^ static_cast<uint32_t>(w[k] >> 32);
+    else if constexpr (PIPE == ZMC_PIPE_FFMA2)
+      acc ^= static_cast<uint32_t>(v[k]) ^ static_cast<uint32_t>(v[k] >> 32);
+    else if constexpr (PIPE == ZMC_PIPE_WIDE_FFMA)
+      acc ^= static_cast<uint32_t>(w[k]) ^ __float_as_uint(f[k]);
+    else if constexpr (PIPE == ZMC_PIPE_WIDE_FFMA2)
+      acc ^= static_cast<uint32_t>(w[k]) ^ static_cast<uint32_t>(v[k]) ^
+             static_cast<uint32_t>(v[k] >> 32);
     else
       acc ^= u[k];
   }
@@ -122,6 +144,9 @@ static PipeKernel pipe_kernel_for(int pipe) {
     case ZMC_PIPE_MUFU_EX2LG2: return pipe_kernel<ZMC_PIPE_MUFU_EX2LG2>;
     case ZMC_PIPE_DFMA: return pipe_kernel<ZMC_PIPE_DFMA>;
     case ZMC_PIPE_PHILOX: return pipe_kernel<ZMC_PIPE_PHILOX>;
+    case ZMC_PIPE_FFMA2: return pipe_kernel<ZMC_PIPE_FFMA2>;
+    case ZMC_PIPE_WIDE_FFMA: return pipe_kernel<ZMC_PIPE_WIDE_FFMA>;
+    case ZMC_PIPE_WIDE_FFMA2: return pipe_kernel<ZMC_PIPE_WIDE_FFMA2>;
     default: return nullptr;
   }
 }
@@ -181,7 +206,7 @@ extern "C" int zmc_pipe_measure(int pipe, int iterations, zmc_pipe_result* out) 
   for (int i = 0; i < blocks; ++i) mean_cyc += static_cast<double>(hc[i]);
   mean_cyc /= blocks;
   delete[] hc;
-  const int per_step = (pipe == ZMC_PIPE_MUFU_EX2LG2) ? 2 : 1;
+  const int per_step = (pipe == ZMC_PIPE_MUFU_EX2LG2 || pipe == ZMC_PIPE_FFMA2) ? 2 : 1;
   const double ops_per_block = static_cast<double>(block) * iterations * kChains * per_step;
   std::memset(out, 0, sizeof(*out));
   out->pipe = pipe;

@@ -116,7 +116,8 @@ class zmc_tune_result(ctypes.Structure):
 
 
 PIPE_NAMES = ["FFMA", "IMAD", "IMAD.WIDE", "IMAD.HI", "LOP3", "SHF", "MUFU.RSQ",
-              "MUFU.EX2+LG2", "DFMA", "PHILOX_CALL", "MUFU.EX2", "MUFU.COS"]
+              "MUFU.EX2+LG2", "DFMA", "PHILOX_CALL", "MUFU.EX2", "MUFU.COS", "FFMA2",
+              "IMAD.WIDE+2FFMA", "IMAD.WIDE+FFMA2"]
 
 # (name, restype, argtypes) of every exported entry point this binding uses.
 SIGNATURES = [
