@@ -141,14 +141,13 @@ def bench_workload(name: str):
 
 
 def traffic_per_launch(spec):
-    """DRAM bytes (read + write) of one sampling-kernel launch from the
-    committed ncu summary; None when the kernel sources changed since the
-    counters were taken.  The summary's figure comes from the 10^5-point cut
-    of the same workload: the partial sums (16 B per unit) stay in L2 for both
-    grid sizes, so the DRAM bytes do not grow with the grid."""
+    """DRAM bytes (read + write) of one full-size sampling-kernel launch of
+    the Gaussian 10^6-point workload, from the committed ncu summary; None
+    for other workloads, or when the kernel sources changed since the
+    counters were taken."""
     from paper_1910_01965_gb300 import build as B
     path = os.path.join(ROOT, "profiles", "scan_kernel_gauss03_N4_fp32k.md")
-    if not os.path.exists(path) or spec.integrand_id != 2 or spec.N != 4:
+    if not os.path.exists(path) or spec.integrand_id != 2 or spec.N != 4 or spec.P != 10**6:
         return None
     stamp = B.source_stamp()
     val, src = None, None
@@ -300,6 +299,7 @@ def serving_run(window_s: float, rate: float = 500.0, large_fraction: float = 0.
            "requests": len(tickets), "large_requests": len(lat["large"]),
            "offered_evals_per_s": evals / window_s,
            "evals_per_s": evals / wall, "gpu_busy_evals_per_s": st.evals_per_s,
+           "utilisation": (evals / window_s) / st.evals_per_s if st.evals_per_s > 0 else 0.0,
            "wall_s": wall, "drain_s": max(0.0, wall - window_s), "steps": st.steps,
            "max_queued": st.max_queued,
            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mem_peak_bytes": st.mem_peak,
@@ -316,10 +316,12 @@ def serving_run(window_s: float, rate: float = 500.0, large_fraction: float = 0.
 
 
 def sustainable(res) -> bool:
-    """A rate is sustainable when the backlog left at the end of the arrival
-    window drains within a quarter of the window: an overloaded queue grows in
-    proportion to the window, a stable one stays near the in-flight work."""
-    return res["drain_s"] <= 0.25 * res["window_s"]
+    """A rate is sustainable when the offered work stays below what the GPU
+    serves per second of busy time under the same mix (utilisation below 1:
+    the queue is stable) and the backlog left at the end of the arrival window
+    drains within a quarter of the window (an overloaded queue grows in
+    proportion to the window, a stable one stays near the in-flight work)."""
+    return res["utilisation"] <= 1.0 and res["drain_s"] <= 0.25 * res["window_s"]
 
 
 def run_serving_sweep(args, world, rank, local):
@@ -334,8 +336,8 @@ def run_serving_sweep(args, world, rank, local):
     clocks.start()
     sweeps = {}
     for name, frac, rates, window in (
-            ("small_only", 0.0, [50, 100, 200, 300, 400, 600], 4.0),
-            ("mix_1pct_large", 0.01, [5, 10, 15, 20, 30], args.serve_window)):
+            ("small_only", 0.0, [50, 100, 125, 150, 175, 200, 250], 4.0),
+            ("mix_1pct_large", 0.01, [10, 20, 30, 35, 40, 45, 50, 60], args.serve_window)):
         pts = []
         best = None
         for r in rates:
@@ -343,7 +345,9 @@ def run_serving_sweep(args, world, rank, local):
             ok = sustainable(res)
             pts.append({k: res[k] for k in (
                 "arrival_rate_per_s", "requests", "large_requests", "evals_per_s",
-                "offered_evals_per_s", "wall_s", "drain_s", "p50_ms", "p99_ms",
+                "offered_evals_per_s", "gpu_busy_evals_per_s", "utilisation", "wall_s",
+                "drain_s", "p50_ms", "p99_ms", "small_p50_ms", "small_p99_ms", "large_p50_ms",
+                "large_p99_ms",
                 "outstanding_max", "outstanding_at_window_end", "max_queued")
                 if k in res} | {"sustainable": ok})
             if ok:

@@ -70,7 +70,8 @@ struct Request {
   int64_t chunk = 0, chunk_first = 0, chunk_count = 0;
   int64_t chunk_units = 0, chunk_tiles = 0, next_tile = 0;
   ScanArgs args{};
-  bool awaiting_last_copy = false;
+  bool awaiting_last_copy = false;  // every tile of the last chunk is launched
+  bool last_copy_issued = false;    // ... and its device->host copy is enqueued
   // shared with API threads (under the server mutex)
   int status = ZMC_OK;
   bool done = false;
@@ -100,9 +101,12 @@ struct zmc_server {
   std::vector<std::shared_ptr<zmc::Request>> active;
   int64_t seq = 0;
   cudaStream_t compute = nullptr, copy = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
-  char* h_stage = nullptr;  // pinned upload staging
-  char* d_stage = nullptr;  // device copy of the step tables
+  // Two steps may be in flight: each has its own pinned staging buffer and
+  // events; the device copy of the step tables is shared, because a step's
+  // upload is ordered after the previous step's kernels on the same stream.
+  cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_end[2] = {nullptr, nullptr};
+  char* h_stage[2] = {nullptr, nullptr};  // pinned upload staging
+  char* d_stage = nullptr;                // device copy of the step tables
   size_t stage_bytes = 0;
   int64_t tile_cap = 0;
   unsigned long long* d_counters = nullptr;
@@ -242,17 +246,51 @@ struct StepPick {
   bool completes_chunk;
 };
 
+// A launched step: its staging slot, work and the chunks it finalizes.
+struct Step {
+  int slot = 0;
+  double evals = 0;
+  std::vector<ChunkDone> completing;
+};
+
+// Wait for a launched step, account its GPU time and enqueue the host copies
+// of the chunks it finalized (on the copy stream, overlapping later steps).
+static void retire_step(zmc_server* s, Step& st) {
+  cudaEventSynchronize(s->ev_end[st.slot]);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, s->ev_start[st.slot], s->ev_end[st.slot]);
+  if (ms > 0.05f && st.evals > 0) s->rate = 0.7 * s->rate + 0.3 * (st.evals / ms);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->busy_ms += ms;
+    s->steps++;
+  }
+  for (auto& c : st.completing) {
+    Request* r = c.r.get();
+    if (r->done || r->cancel.load()) continue;
+    if (copy_chunk(s, c) != ZMC_OK) {
+      r->cancel.store(true);
+      continue;
+    }
+    if (c.chunk == r->nchunks - 1) r->last_copy_issued = true;
+  }
+}
+
 // ------------------------------------------------------------ one step --
 static void run_loop(zmc_server* s) {
   cudaSetDevice(s->device);
-  std::vector<ChunkDone> to_copy;
+  // Steps are pipelined two deep: after launching step k the scheduler
+  // retires step k-1 (waits for it, enqueues its copies) and then plans step
+  // k+1 while step k runs, so the GPU does not idle during host work.
+  std::deque<Step> inflight;
+  int slot = 0;
   for (;;) {
     // 1. queue -> active, cancellations, stop.
     bool stopping;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       stopping = s->stop;
-      if (!stopping && s->queue.empty() && s->active.empty() && to_copy.empty())
+      if (!stopping && s->queue.empty() && s->active.empty() && inflight.empty())
         s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
       stopping = s->stop;
     }
@@ -293,18 +331,21 @@ static void run_loop(zmc_server* s) {
       }
     }
     if (stopping && s->active.empty()) {
+      while (!inflight.empty()) {
+        retire_step(s, inflight.front());
+        inflight.pop_front();
+      }
       cudaStreamSynchronize(s->copy);
       return;
     }
-    // 2. pick tiles (skip cancelled and finished-issuing requests)
+    // 2. pick tiles (skip cancelled requests and those with every tile launched)
     std::vector<StepPick> picks;
     double budget = std::max(1.0, s->opts.step_ms * s->rate);
     int64_t tiles_used = 0;
     {
       std::vector<std::shared_ptr<Request>> ready;
       for (auto& r : s->active)
-        if (!r->cancel.load() && !stopping && !r->awaiting_last_copy &&
-            r->next_tile < r->chunk_tiles)
+        if (!r->cancel.load() && !stopping && r->next_tile < r->chunk_tiles)
           ready.push_back(r);
       std::shared_ptr<Request> oldest;
       for (auto& r : ready)
@@ -340,14 +381,13 @@ static void run_loop(zmc_server* s) {
       }
     }
     // 3. upload and launch the step
-    double step_evals = 0;
-    std::vector<ChunkDone> completing;
-    bool launched = false;
     if (!picks.empty()) {
+      Step st;
+      st.slot = slot;
       const int nsc = static_cast<int>(picks.size());
       std::vector<FinalizeArgs> fa;
       std::vector<int64_t> prefix(1, 0);
-      char* h = s->h_stage;
+      char* h = s->h_stage[slot];
       ScanArgs* h_args = reinterpret_cast<ScanArgs*>(h);
       const size_t off_tiles = s256(sizeof(ScanArgs) * s->opts.max_active);
       BatchTile* h_tiles = reinterpret_cast<BatchTile*>(h + off_tiles);
@@ -383,8 +423,8 @@ static void run_loop(zmc_server* s) {
         const int G = group_samples(r->d.N);
         const int64_t per_block = kServeBlock / r->tp.lanes;
         const int64_t groups = (r->args.ngroups + r->tp.splits - 1) / r->tp.splits;
-        step_evals += static_cast<double>(picks[i].tile_end - picks[i].tile_begin) *
-                      per_block * groups * G;
+        st.evals += static_cast<double>(picks[i].tile_end - picks[i].tile_begin) *
+                    per_block * groups * G;
         if (picks[i].completes_chunk) {
           const int buf = static_cast<int>(r->chunk % 2);
           if (r->copy_pending[buf]) {  // the buffer's previous chunk must be in host memory
@@ -406,16 +446,15 @@ static void run_loop(zmc_server* s) {
           f.s2 = r->o.s2 ? base + 3 * n + n * T : nullptr;
           fa.push_back(f);
           prefix.push_back(prefix.back() + n);
-          completing.push_back(ChunkDone{picks[i].r, r->chunk, r->chunk_first, n, buf});
+          st.completing.push_back(ChunkDone{picks[i].r, r->chunk, r->chunk_first, n, buf});
         }
       }
       for (size_t k = 0; k < fa.size(); ++k) h_fa[k] = fa[k];
       for (size_t k = 0; k < prefix.size(); ++k) h_pre[k] = prefix[k];
       const size_t upload = off_pre + prefix.size() * sizeof(int64_t);
-      cudaError_t e = cudaMemcpyAsync(s->d_stage, s->h_stage, upload, cudaMemcpyHostToDevice,
-                                      s->compute);
+      cudaError_t e = cudaMemcpyAsync(s->d_stage, h, upload, cudaMemcpyHostToDevice, s->compute);
       int rc = e == cudaSuccess ? ZMC_OK : ZMC_ECUDA;
-      cudaEventRecord(s->ev_start, s->compute);
+      cudaEventRecord(s->ev_start[slot], s->compute);
       for (int prec = 0; prec < 3 && rc == ZMC_OK; ++prec) {
         if (gend[prec] == gbeg[prec]) continue;
         unsigned long long* cnt = s->d_counters + 32 * prec;
@@ -442,71 +481,54 @@ static void run_loop(zmc_server* s) {
         fb.total = prefix.back();
         if (finalize_batch_launch(fb, s->compute) != 0) rc = ZMC_ECUDA;
       }
-      cudaEventRecord(s->ev_end, s->compute);
-      launched = true;
+      cudaEventRecord(s->ev_end[slot], s->compute);
       if (rc != ZMC_OK) {
         for (auto& p : picks) p.r->cancel.store(true);  // fail what the step carried
+        cudaStreamSynchronize(s->compute);
         for (auto& p : picks) {
-          cudaStreamSynchronize(s->compute);
           release_device(s, p.r.get());
           finish_request(s, p.r, ZMC_ECUDA);
         }
         s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
                                        [](const std::shared_ptr<Request>& r) { return r->done; }),
                         s->active.end());
-        picks.clear();
-        completing.clear();
+      } else {
+        // the next chunk of a request may be picked by the next step: its
+        // tiles run after this step's finalize on the same stream
+        for (auto& c : st.completing) {
+          Request* r = c.r.get();
+          if (c.chunk + 1 < r->nchunks)
+            start_chunk(r, c.chunk + 1);
+          else
+            r->awaiting_last_copy = true;
+        }
+        inflight.push_back(std::move(st));
+        slot ^= 1;
       }
-    }
-    // 4. while the step runs: copies of the previous step's chunks
-    for (auto& c : to_copy)
-      if (!c.r->cancel.load() && copy_chunk(s, c) != ZMC_OK) c.r->cancel.store(true);
-    to_copy.clear();
-    // 5. wait for the step, account, advance chunks
-    if (launched) {
-      cudaEventSynchronize(s->ev_end);
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, s->ev_start, s->ev_end);
-      if (ms > 0.05f && step_evals > 0) s->rate = 0.7 * s->rate + 0.3 * (step_evals / ms);
-      {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->busy_ms += ms;
-        s->steps++;
+      // 4. keep one step queued behind the running one
+      while (inflight.size() >= 2) {
+        retire_step(s, inflight.front());
+        inflight.pop_front();
       }
-      for (auto& c : completing) {
-        Request* r = c.r.get();
-        to_copy.push_back(c);
-        if (c.chunk + 1 < r->nchunks)
-          start_chunk(r, c.chunk + 1);
-        else
-          r->awaiting_last_copy = true;
-      }
-    } else if (!to_copy.empty() || s->active.empty()) {
+    } else if (!inflight.empty()) {
+      retire_step(s, inflight.front());
+      inflight.pop_front();
+    } else {
       // nothing to compute: let pending copies finish
       cudaStreamSynchronize(s->copy);
-    } else {
-      cudaStreamSynchronize(s->copy);
     }
-    // requests whose last chunk reached host memory, and cancellations
+    // 5. requests whose last chunk reached host memory, and cancellations
     std::vector<std::shared_ptr<Request>> keep;
     for (auto& r : s->active) {
-      const int last_buf = static_cast<int>((r->nchunks - 1) % 2);
-      const bool in_to_copy = std::any_of(to_copy.begin(), to_copy.end(),
-                                          [&](const ChunkDone& c) { return c.r == r; });
       if (r->cancel.load() || stopping) {
-        if (in_to_copy) {
-          to_copy.erase(std::remove_if(to_copy.begin(), to_copy.end(),
-                                       [&](const ChunkDone& c) { return c.r == r; }),
-                        to_copy.end());
-        }
         cudaStreamSynchronize(s->copy);
         cudaStreamSynchronize(s->compute);
         release_device(s, r.get());
         finish_request(s, r, ZMC_ECANCELED);
         continue;
       }
-      if (r->awaiting_last_copy && !in_to_copy && r->copy_pending[last_buf] &&
-          cudaEventQuery(r->copied[last_buf]) == cudaSuccess) {
+      const int last_buf = static_cast<int>((r->nchunks - 1) % 2);
+      if (r->last_copy_issued && cudaEventQuery(r->copied[last_buf]) == cudaSuccess) {
         release_device(s, r.get());
         finish_request(s, r, ZMC_OK);
         continue;
@@ -555,16 +577,23 @@ int zmc_server_create(size_t mem_budget_bytes, const zmc_server_opts* opts, zmc_
                    s256(sizeof(int64_t) * (o.max_active + 1));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_start);
-  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_end);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_stage), s->stage_bytes, 0);
+  for (int k = 0; k < 2; ++k) {
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev_start[k]);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev_end[k]);
+    if (e == cudaSuccess)
+      e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_stage[k]), s->stage_bytes, 0);
+  }
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_stage), s->stage_bytes);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->d_counters), 3 * 256);
   if (e != cudaSuccess) {
     int rc = cuda_fail(e, "server set-up");
     if (s->d_counters) cudaFree(s->d_counters);
     if (s->d_stage) cudaFree(s->d_stage);
-    if (s->h_stage) cudaFreeHost(s->h_stage);
+    for (int k = 0; k < 2; ++k) {
+      if (s->h_stage[k]) cudaFreeHost(s->h_stage[k]);
+      if (s->ev_start[k]) cudaEventDestroy(s->ev_start[k]);
+      if (s->ev_end[k]) cudaEventDestroy(s->ev_end[k]);
+    }
     if (s->compute) cudaStreamDestroy(s->compute);
     if (s->copy) cudaStreamDestroy(s->copy);
     delete s;
@@ -731,9 +760,11 @@ int zmc_server_destroy(zmc_server* s) {
   cudaStreamSynchronize(s->copy);
   cudaFree(s->d_counters);
   cudaFree(s->d_stage);
-  cudaFreeHost(s->h_stage);
-  cudaEventDestroy(s->ev_start);
-  cudaEventDestroy(s->ev_end);
+  for (int k = 0; k < 2; ++k) {
+    cudaFreeHost(s->h_stage[k]);
+    cudaEventDestroy(s->ev_start[k]);
+    cudaEventDestroy(s->ev_end[k]);
+  }
   cudaStreamDestroy(s->compute);
   cudaStreamDestroy(s->copy);
   delete s;
