@@ -140,25 +140,28 @@ def bench_workload(name: str):
             "cosprod_100": wl.scan_cosprod_100}[name]()
 
 
-def traffic_per_launch(spec):
-    """DRAM bytes (read + write) of one full-size sampling-kernel launch of
-    the Gaussian 10^6-point workload, from the committed ncu summary; None
-    for other workloads, or when the kernel sources changed since the
-    counters were taken."""
+def profile_figures(spec):
+    """`key: value` figures of the committed ncu summary of the sampling kernel
+    on the Gaussian 10^6-point workload (DRAM bytes of one full-size launch,
+    FMA-heavy pipe cycles per evaluation); {} for other workloads, or when the
+    kernel sources changed since the counters were taken."""
     from paper_1910_01965_gb300 import build as B
     path = os.path.join(ROOT, "profiles", "scan_kernel_gauss03_N4_fp32k.md")
     if not os.path.exists(path) or spec.integrand_id != 2 or spec.N != 4 or spec.P != 10**6:
-        return None
-    stamp = B.source_stamp()
-    val, src = None, None
+        return {}
+    figs, src = {}, None
     for line in open(path):
-        if line.startswith("traffic_bytes_per_launch:"):
-            val = float(line.split(":", 1)[1].split()[0])
-        if line.startswith("kernel_source_stamp:"):
-            src = line.split(":", 1)[1].strip()
-    if val is None or src != stamp:
-        return None
-    return val
+        key, sep, rest = line.partition(":")
+        if not sep or " " in key:
+            continue
+        if key == "kernel_source_stamp":
+            src = rest.strip()
+        else:
+            try:
+                figs[key] = float(rest.split()[0])
+            except (ValueError, IndexError):
+                pass
+    return figs if src == B.source_stamp() else {}
 
 
 # ------------------------------------------------------------- CPU oracle --
@@ -839,12 +842,22 @@ def main():
         f_max, f_src = info.clock_khz / 1e3, "device-reported maximum SM clock"
     peak = info.sm_count * 128 * f_max * 1e6 / 1e12   # lane-ops per second, T
     achieved = ops / (k_ms * 1e-3) / 1e12
+    figs = profile_figures(spec) if prec == zmc.ZMC_FP32_KAHAN else {}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": traffic_per_launch(spec),
+                "frac": achieved / peak, "traffic": figs.get("traffic_bytes_per_launch"),
                 "kernel": "scan_kernel (sampling)", "kernel_ms": k_ms,
                 "ops_per_eval": ops_per_eval(spec.integrand_id, spec.N, prec),
                 "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s)" % (
                     info.sm_count, f_max, f_src)}
+    if "heavy_smsp_cycles_per_eval" in figs:
+        # the pipe that binds: each SMSP's FMA-heavy pipe, cycles per evaluation
+        # from the committed ncu counters; its ceiling at the same clock
+        cyc = figs["heavy_smsp_cycles_per_eval"]
+        ceil = info.sm_count * 4 * f_max * 1e6 / cyc
+        kernel_rate = spec.evals / (k_ms * 1e-3)
+        roofline["binding_pipe"] = {"pipe": "FMA-heavy", "smsp_cycles_per_eval": cyc,
+                                    "evals_per_s_at_full_pipe": ceil,
+                                    "frac": kernel_rate / ceil}
 
     # end to end through the C ABI with host buffers (pinned)
     h_vals = torch.tensor(spec.values, dtype=torch.float64).pin_memory().numpy()

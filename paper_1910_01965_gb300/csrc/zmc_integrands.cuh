@@ -26,10 +26,6 @@
 
 #include <cstdint>
 
-#ifndef ZMC_F32X2
-#define ZMC_F32X2 0  // 1: FP32 functors and compensated sums use packed f32x2 pairs
-#endif
-
 namespace zmc {
 
 constexpr double kOneMinusHalfUlp = 1.0 - 0x1p-24;     // 1 - 2^-24
@@ -56,45 +52,6 @@ __device__ __forceinline__ double unit_u64(uint32_t r) {
       static_cast<long long>(0x3FF0000000000000ull |
                              (static_cast<uint64_t>(r >> 9) << 29)));
   return d - kOneMinusHalfUlp;
-}
-
-// Packed FP32 pairs (f32x2, Blackwell): one instruction applies the same
-// correctly rounded operation to the two floats of a 64-bit register pair, so
-// each half equals the scalar operation bit for bit.
-__device__ __forceinline__ uint64_t pk(float lo, float hi) {
-  uint64_t v;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
-  return v;
-}
-__device__ __forceinline__ float pk_lo(uint64_t v) {
-  return __uint_as_float(static_cast<uint32_t>(v));
-}
-__device__ __forceinline__ float pk_hi(uint64_t v) {
-  return __uint_as_float(static_cast<uint32_t>(v >> 32));
-}
-__device__ __forceinline__ void set_half(uint64_t& v, int hi, float x) {
-  const uint64_t b = __float_as_uint(x);
-  v = hi ? ((v & 0xffffffffull) | (b << 32)) : ((v & ~0xffffffffull) | b);
-}
-__device__ __forceinline__ uint64_t fma_x2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ uint64_t mul_x2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t add_x2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t sub_x2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
 }
 
 __device__ __forceinline__ float ex2_approx(float v) {
@@ -274,43 +231,13 @@ struct CosProd32 {
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  float B[N], C[N];
   static __device__ float2 value(int, double x, double a, double b) {
     const double w = b - a;
     return make_float2(static_cast<float>(x * w),
                        static_cast<float>(x * (a - w * kOneMinusHalfUlp)));
   }
   static __device__ void dim(int, double, double, float*) {}
-#if ZMC_F32X2
-  static constexpr int kP = N / 2;
-  uint64_t B2[kP > 0 ? kP : 1], C2[kP > 0 ? kP : 1];
-  float Bt, Ct;  // dimension N-1 when N is odd
-  __device__ void load(int k, float2 v, const float*) {
-    if (k < 2 * kP) {
-      set_half(B2[k >> 1], k & 1, v.x);
-      set_half(C2[k >> 1], k & 1, v.y);
-    } else {
-      Bt = v.x;
-      Ct = v.y;
-    }
-  }
-  __device__ float eval(const uint32_t* r) const {
-    if constexpr (kP == 0) {
-      return __cosf(fmaf(Bt, unit_f12(r[0]), Ct));
-    } else {
-      uint64_t a = fma_x2(B2[0], pk(unit_f12(r[0]), unit_f12(r[1])), C2[0]);
-      uint64_t g2 = pk(__cosf(pk_lo(a)), __cosf(pk_hi(a)));
-#pragma unroll
-      for (int k = 1; k < kP; ++k) {
-        a = fma_x2(B2[k], pk(unit_f12(r[2 * k]), unit_f12(r[2 * k + 1])), C2[k]);
-        g2 = mul_x2(g2, pk(__cosf(pk_lo(a)), __cosf(pk_hi(a))));
-      }
-      float g = pk_lo(g2) * pk_hi(g2);
-      if constexpr (N % 2) g *= __cosf(fmaf(Bt, unit_f12(r[N - 1]), Ct));
-      return g;
-    }
-  }
-#else
-  float B[N], C[N];
   __device__ void load(int k, float2 v, const float*) { B[k] = v.x; C[k] = v.y; }
   __device__ float eval(const uint32_t* r) const {
     float g = __cosf(fmaf(B[0], unit_f12(r[0]), C[0]));
@@ -318,7 +245,6 @@ struct CosProd32 {
     for (int k = 1; k < N; ++k) g *= __cosf(fmaf(B[k], unit_f12(r[k]), C[k]));
     return g;
   }
-#endif
 };
 
 // exp(-(y-x)^2/(2 s^2)) per dimension = 2^-(d^2), d = c (y - x) = B f + C,
@@ -329,6 +255,7 @@ struct Gauss32 {
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  float B[N], C[N];
   static __device__ float2 value(int, double x, double a, double b) {
     const double w = b - a;
     return make_float2(static_cast<float>((a - w * kOneMinusHalfUlp - x) * kGaussScale), 0.f);
@@ -336,44 +263,6 @@ struct Gauss32 {
   static __device__ void dim(int, double a, double b, float* out) {
     out[0] = static_cast<float>((b - a) * kGaussScale);
   }
-#if ZMC_F32X2
-  // Dimensions in packed pairs (2k, 2k+1): d = B f + C and the sum of d^2
-  // run two dimensions per instruction; the two halves meet at the end.
-  static constexpr int kP = N / 2;
-  uint64_t B2[kP > 0 ? kP : 1], C2[kP > 0 ? kP : 1];
-  float Bt, Ct;  // dimension N-1 when N is odd
-  __device__ void load(int k, float2 v, const float* d) {
-    if (k < 2 * kP) {
-      set_half(B2[k >> 1], k & 1, d[0]);
-      set_half(C2[k >> 1], k & 1, v.x);
-    } else {
-      Bt = d[0];
-      Ct = v.x;
-    }
-  }
-  __device__ float eval(const uint32_t* r) const {
-    float q;
-    if constexpr (kP > 0) {
-      uint64_t d = fma_x2(B2[0], pk(unit_f12(r[0]), unit_f12(r[1])), C2[0]);
-      uint64_t q2 = mul_x2(d, d);
-#pragma unroll
-      for (int k = 1; k < kP; ++k) {
-        d = fma_x2(B2[k], pk(unit_f12(r[2 * k]), unit_f12(r[2 * k + 1])), C2[k]);
-        q2 = fma_x2(d, d, q2);
-      }
-      q = pk_lo(q2) + pk_hi(q2);
-      if constexpr (N % 2) {
-        const float e = fmaf(Bt, unit_f12(r[N - 1]), Ct);
-        q = fmaf(e, e, q);
-      }
-    } else {
-      const float e = fmaf(Bt, unit_f12(r[0]), Ct);
-      q = e * e;
-    }
-    return ex2_approx(-q);
-  }
-#else
-  float B[N], C[N];
   __device__ void load(int k, float2 v, const float* d) { B[k] = d[0]; C[k] = v.x; }
   __device__ float eval(const uint32_t* r) const {
     float d = fmaf(B[0], unit_f12(r[0]), C[0]);
@@ -385,7 +274,6 @@ struct Gauss32 {
     }
     return ex2_approx(-q);
   }
-#endif
 };
 
 // prod (1 + x y^2), y = W f + A (per dimension), X = x (per value).
@@ -395,6 +283,7 @@ struct Poly32 {
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  float W[N], A[N], X[N];
   static __device__ float2 value(int, double x, double, double) {
     return make_float2(static_cast<float>(x), 0.f);
   }
@@ -403,44 +292,6 @@ struct Poly32 {
     out[0] = static_cast<float>(w);
     out[1] = static_cast<float>(a - w * kOneMinusHalfUlp);
   }
-#if ZMC_F32X2
-  static constexpr int kP = N / 2;
-  uint64_t W2[kP > 0 ? kP : 1], A2[kP > 0 ? kP : 1], X2[kP > 0 ? kP : 1];
-  float Wt, At, Xt;  // dimension N-1 when N is odd
-  __device__ void load(int k, float2 v, const float* d) {
-    if (k < 2 * kP) {
-      set_half(W2[k >> 1], k & 1, d[0]);
-      set_half(A2[k >> 1], k & 1, d[1]);
-      set_half(X2[k >> 1], k & 1, v.x);
-    } else {
-      Wt = d[0];
-      At = d[1];
-      Xt = v.x;
-    }
-  }
-  __device__ float eval(const uint32_t* r) const {
-    if constexpr (kP == 0) {
-      const float y = fmaf(Wt, unit_f12(r[0]), At);
-      return fmaf(Xt * y, y, 1.0f);
-    } else {
-      const uint64_t one2 = pk(1.0f, 1.0f);
-      uint64_t y = fma_x2(W2[0], pk(unit_f12(r[0]), unit_f12(r[1])), A2[0]);
-      uint64_t g2 = fma_x2(mul_x2(X2[0], y), y, one2);
-#pragma unroll
-      for (int k = 1; k < kP; ++k) {
-        y = fma_x2(W2[k], pk(unit_f12(r[2 * k]), unit_f12(r[2 * k + 1])), A2[k]);
-        g2 = mul_x2(g2, fma_x2(mul_x2(X2[k], y), y, one2));
-      }
-      float g = pk_lo(g2) * pk_hi(g2);
-      if constexpr (N % 2) {
-        const float yt = fmaf(Wt, unit_f12(r[N - 1]), At);
-        g *= fmaf(Xt * yt, yt, 1.0f);
-      }
-      return g;
-    }
-  }
-#else
-  float W[N], A[N], X[N];
   __device__ void load(int k, float2 v, const float* d) { W[k] = d[0]; A[k] = d[1]; X[k] = v.x; }
   __device__ float eval(const uint32_t* r) const {
     float y = fmaf(W[0], unit_f12(r[0]), A[0]);
@@ -452,7 +303,6 @@ struct Poly32 {
     }
     return g;
   }
-#endif
 };
 
 // cos(sum_k y_k (x_k + 0.1 y_k)), y = W f + A (per dimension), X = x.
@@ -462,6 +312,7 @@ struct Osc32 {
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  float W[N], A[N], X[N];
   static __device__ float2 value(int, double x, double, double) {
     return make_float2(static_cast<float>(x), 0.f);
   }
@@ -470,46 +321,6 @@ struct Osc32 {
     out[0] = static_cast<float>(w);
     out[1] = static_cast<float>(a - w * kOneMinusHalfUlp);
   }
-#if ZMC_F32X2
-  static constexpr int kP = N / 2;
-  uint64_t W2[kP > 0 ? kP : 1], A2[kP > 0 ? kP : 1], X2[kP > 0 ? kP : 1];
-  float Wt, At, Xt;  // dimension N-1 when N is odd
-  __device__ void load(int k, float2 v, const float* d) {
-    if (k < 2 * kP) {
-      set_half(W2[k >> 1], k & 1, d[0]);
-      set_half(A2[k >> 1], k & 1, d[1]);
-      set_half(X2[k >> 1], k & 1, v.x);
-    } else {
-      Wt = d[0];
-      At = d[1];
-      Xt = v.x;
-    }
-  }
-  __device__ float eval(const uint32_t* r) const {
-    const float q = static_cast<float>(kOscQuad);
-    float ph;
-    if constexpr (kP == 0) {
-      const float y = fmaf(Wt, unit_f12(r[0]), At);
-      ph = y * fmaf(q, y, Xt);
-    } else {
-      const uint64_t q2 = pk(q, q);
-      uint64_t y = fma_x2(W2[0], pk(unit_f12(r[0]), unit_f12(r[1])), A2[0]);
-      uint64_t ph2 = mul_x2(y, fma_x2(q2, y, X2[0]));
-#pragma unroll
-      for (int k = 1; k < kP; ++k) {
-        y = fma_x2(W2[k], pk(unit_f12(r[2 * k]), unit_f12(r[2 * k + 1])), A2[k]);
-        ph2 = fma_x2(y, fma_x2(q2, y, X2[k]), ph2);
-      }
-      ph = pk_lo(ph2) + pk_hi(ph2);
-      if constexpr (N % 2) {
-        const float yt = fmaf(Wt, unit_f12(r[N - 1]), At);
-        ph = fmaf(yt, fmaf(q, yt, Xt), ph);
-      }
-    }
-    return __cosf(ph);
-  }
-#else
-  float W[N], A[N], X[N];
   __device__ void load(int k, float2 v, const float* d) { W[k] = d[0]; A[k] = d[1]; X[k] = v.x; }
   __device__ float eval(const uint32_t* r) const {
     float y = fmaf(W[0], unit_f12(r[0]), A[0]);
@@ -521,7 +332,6 @@ struct Osc32 {
     }
     return __cosf(ph);
   }
-#endif
 };
 
 // sin(sum_k W_k f_k + C0), C0 = (sum_k A_k + sum_l x_l) reduced mod 2 pi in FP64.
@@ -547,18 +357,6 @@ struct SinSum32 {
     C0 = static_cast<float>(c);
   }
   __device__ float eval(const uint32_t* r) const {
-#if ZMC_F32X2
-    if constexpr (N >= 2) {
-      // even and odd dimensions as the two halves of a packed sum
-      uint64_t s2 = fma_x2(pk(W[0], W[1]), pk(unit_f12(r[0]), unit_f12(r[1])), pk(C0, 0.0f));
-#pragma unroll
-      for (int k = 2; k + 1 < N; k += 2)
-        s2 = fma_x2(pk(W[k], W[k + 1]), pk(unit_f12(r[k]), unit_f12(r[k + 1])), s2);
-      float s = pk_lo(s2) + pk_hi(s2);
-      if constexpr (N % 2) s = fmaf(W[N - 1], unit_f12(r[N - 1]), s);
-      return __sinf(s);
-    }
-#endif
     float s = C0;
 #pragma unroll
     for (int k = 0; k < N; ++k) s = fmaf(W[k], unit_f12(r[k]), s);

@@ -41,8 +41,8 @@ enum { kPrecFP64 = ZMC_FP64, kPrecFP32 = ZMC_FP32, kPrecFP32K = ZMC_FP32_KAHAN }
 #ifndef ZMC_PAIR_GROUPS
 #define ZMC_PAIR_GROUPS 4    // groups in flight per lane when G == 1 (2 or 4)
 #endif
-#ifndef ZMC_SWP
-#define ZMC_SWP 0            // 1: draw the next block of groups before summing this one
+#ifndef ZMC_EVEN_GROUPS
+#define ZMC_EVEN_GROUPS 4    // groups per block when G is even and a group is one call
 #endif
 
 template <int PREC>
@@ -82,29 +82,6 @@ struct LaneAcc<kPrecFP32> {
 // sum is s - c, taken in FP64.
 template <>
 struct LaneAcc<kPrecFP32K> {
-#if ZMC_F32X2
-  // (s1, s2) and the negated compensations (-c1, -c2) as packed pairs: both
-  // compensated additions take four packed instructions, and each half is
-  // the scalar Kahan step below bit for bit (a - c == a + (-c) exactly).
-  uint64_t s = 0, cn = 0;
-  __device__ __forceinline__ void add_y(uint64_t y) {
-    const uint64_t t = add_x2(s, y);
-    cn = sub_x2(y, sub_x2(t, s));
-    s = t;
-  }
-  __device__ __forceinline__ void add(float g) {
-    add_y(fma_x2(pk(g, g), pk(1.0f, g), cn));  // (g - c1, g*g - c2)
-  }
-  __device__ __forceinline__ void add2(float a, float b) {
-    add_y(add_x2(pk(a + b, fmaf(a, a, b * b)), cn));
-  }
-  __device__ __forceinline__ double sum1() const {
-    return static_cast<double>(pk_lo(s)) + static_cast<double>(pk_lo(cn));
-  }
-  __device__ __forceinline__ double sum2() const {
-    return static_cast<double>(pk_hi(s)) + static_cast<double>(pk_hi(cn));
-  }
-#else
   float s1 = 0.0f, c1 = 0.0f, s2 = 0.0f, c2 = 0.0f;
   __device__ __forceinline__ void add(float g) {
     const float y1 = g - c1;
@@ -137,7 +114,6 @@ struct LaneAcc<kPrecFP32K> {
   __device__ __forceinline__ double sum2() const {
     return static_cast<double>(s2) - static_cast<double>(c2);
   }
-#endif
 };
 
 // List that staged value `idx` belongs to.
@@ -234,6 +210,12 @@ __device__ __forceinline__ const void* stage_lists(const ScanArgs& a, double* sm
 }
 
 // Sum over the sample groups [q, q_end) with stride `step` (one lane).
+//
+// Order of the compensated additions (the same for every blocking choice
+// below, so the single-scan and batched kernels agree bit for bit): with G
+// even, each group's samples enter as pairs (0,1), (2,3), ... in group order;
+// with G odd (G == 1), consecutive groups are paired and a last unpaired
+// group enters alone.
 template <int N, class F, int PREC>
 __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
                                             const uint32_t* __restrict__ rk1,
@@ -251,86 +233,66 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
   StridedProduct sp[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) sp[c].init(q * C + c, step * C);
-  if constexpr (ZMC_KAHAN_PAIRS && (G % 2 == 0 || kUnroll % 2 == 0)) {
-    // Samples enter the sums two at a time.
-    constexpr int U = (G % 2 == 0) ? 1 : ZMC_PAIR_GROUPS;
-    // Draw the words of U groups, then evaluate and sum them.
-    auto draw = [&](uint32_t (&r)[U][4 * C]) {
+  // Draw the words of V consecutive groups of this lane.
+  auto draw = [&](auto& r) {
+    constexpr int V = sizeof(r) / sizeof(r[0]);
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+    for (int u = 0; u < V; ++u)
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[u][4 * c]);
-          sp[c].advance();
-        }
-    };
-    auto consume = [&](const uint32_t (&r)[U][4 * C]) {
-      if constexpr (U == 1) {
-#pragma unroll
-        for (int g = 0; g < G; g += 2) acc.add2(f.eval(&r[0][g * N]), f.eval(&r[0][(g + 1) * N]));
-      } else {
-#pragma unroll
-        for (int u = 0; u < U; u += 2)
-#pragma unroll
-          for (int g = 0; g < G; ++g) acc.add2(f.eval(&r[u][g * N]), f.eval(&r[u + 1][g * N]));
+      for (int c = 0; c < C; ++c) {
+        philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[u][4 * c]);
+        sp[c].advance();
       }
+  };
+  if constexpr (ZMC_KAHAN_PAIRS && G % 2 == 0) {
+    // Pairs within each group.  With one call per group (N = 1, 2) a block
+    // of U groups puts U independent Philox chains in flight per lane.
+    constexpr int U = C == 1 ? ZMC_EVEN_GROUPS : 1;
+    auto consume = [&](const auto& r) {
+      constexpr int V = sizeof(r) / sizeof(r[0]);
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+#pragma unroll
+        for (int g = 0; g < G; g += 2)
+          acc.add2(f.eval(&r[u][g * N]), f.eval(&r[u][(g + 1) * N]));
     };
-#if ZMC_SWP
-    // Software pipelined: the words of the next U groups are drawn before the
-    // current ones are evaluated, so the integer multiplies of one block and
-    // the floating-point work of the previous one are in flight together.
-    // Two buffers in turn (no register copies); the order of the sums is
-    // that of the plain loop below.
-    if (q + (U - 1) * step < q_end) {
-      uint32_t ra[U][4 * C], rb[U][4 * C];
-      draw(ra);
-      q += U * step;
-      for (;;) {
-        if (!(q + (U - 1) * step < q_end)) {
-          consume(ra);
-          break;
-        }
-        draw(rb);
-        q += U * step;
-        consume(ra);
-        if (!(q + (U - 1) * step < q_end)) {
-          consume(rb);
-          break;
-        }
-        draw(ra);
-        q += U * step;
-        consume(rb);
-      }
-    }
-#else
     for (; q + (U - 1) * step < q_end; q += U * step) {
       uint32_t r[U][4 * C];
       draw(r);
       consume(r);
     }
-#endif
-    // Fewer than U groups left: pairs, then a single group, so that the order
-    // of the compensated additions is the same for any U.
+    if constexpr (U > 1) {
+      for (; q < q_end; q += step) {
+        uint32_t r[1][4 * C];
+        draw(r);
+        consume(r);
+      }
+    }
+  } else if constexpr (ZMC_KAHAN_PAIRS && kUnroll % 2 == 0) {
+    // G == 1: consecutive groups are paired; U groups (U/2 pairs) per block.
+    constexpr int U = ZMC_PAIR_GROUPS;
+    auto consume = [&](const auto& r) {
+      constexpr int V = sizeof(r) / sizeof(r[0]);
+#pragma unroll
+      for (int u = 0; u < V; u += 2) acc.add2(f.eval(&r[u][0]), f.eval(&r[u + 1][0]));
+    };
+    for (; q + (U - 1) * step < q_end; q += U * step) {
+      uint32_t r[U][4 * C];
+      draw(r);
+      consume(r);
+    }
+    // Fewer than U groups left: pairs, then a single group.
     if constexpr (U > 2) {
       for (; q + step < q_end; q += 2 * step) {
         uint32_t r[2][4 * C];
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[u][4 * c]);
-            sp[c].advance();
-          }
-#pragma unroll
-        for (int g = 0; g < G; ++g) acc.add2(f.eval(&r[0][g * N]), f.eval(&r[1][g * N]));
+        draw(r);
+        consume(r);
       }
     }
     if (q < q_end) {
-      uint32_t r[4 * C];
-#pragma unroll
-      for (int c = 0; c < C; ++c) philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[4 * c]);
-#pragma unroll
-      for (int g = 0; g < G; ++g) acc.add(f.eval(&r[g * N]));
+      uint32_t r[1][4 * C];
+      draw(r);
+      acc.add(f.eval(&r[0][0]));
     }
   } else {
 #pragma unroll kUnroll

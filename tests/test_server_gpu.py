@@ -104,6 +104,38 @@ def test_chunked_streaming_of_a_large_grid(z):
         srv.close()
 
 
+def test_many_chunks_of_two_grids_interleaved(z):
+    # Small chunks and short steps: each request's chunks finish in consecutive
+    # steps, so both output buffers are reused many times while earlier chunks
+    # are still being copied to the host.  Every output equals the solo run.
+    srv = z.Server(1 << 30, chunk_units=1 << 10, step_ms=0.5)
+    a = wl.ScanSpec("chunks_a", wl.G_COSPROD, 2, np.zeros(2), np.ones(2),
+                    [np.linspace(0.5, 5, 97), np.linspace(0.5, 5, 61)], 256, 3, 11)
+    b = wl.ScanSpec("chunks_b", wl.G_POLY, 1, np.zeros(1), np.ones(1),
+                    [np.linspace(0.5, 5, 7919)], 128, 2, 12)
+    try:
+        ta = srv.submit(a.integrand_id, a.N, a.lo, a.hi, a.lengths, a.values, a.samples,
+                        a.trials, a.seed, 2, want_sums=True)
+        tb = srv.submit(b.integrand_id, b.N, b.lo, b.hi, b.lengths, b.values, b.samples,
+                        b.trials, b.seed, 0, want_sums=True)
+        assert srv.wait(ta, 120000) == z.ZMC_OK and srv.wait(tb, 120000) == z.ZMC_OK
+        chunks = []
+        for t, spec, prec in ((ta, a, 2), (tb, b, 0)):
+            res, o = srv.result(t)
+            per_chunk = max(1, 1024 // (spec.trials * o.tile_splits))
+            chunks.append(-(-spec.P // per_chunk))
+            solo, so = z.scan(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                              spec.values, spec.samples, spec.trials, spec.seed,
+                              precision=prec, tiles=(o.tile_lanes, o.tile_splits, 256),
+                              want_sums=True)
+            for k in ("mean", "err", "errw", "s1", "s2"):
+                assert np.array_equal(res[k], solo[k]), (spec.name, k)
+        # 1024 unit-splits per chunk; a request finishes at most one chunk a step
+        assert min(chunks) > 8 and srv.stats().steps >= max(chunks)
+    finally:
+        srv.close()
+
+
 def test_cancel_and_timeouts(z):
     srv = z.Server(1 << 30, step_ms=1.0, max_active=4)
     big = wl.scan_gauss_1e6(samples=1 << 14)  # ~0.2 s of GPU work
