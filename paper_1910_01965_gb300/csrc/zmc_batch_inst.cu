@@ -10,11 +10,15 @@
 // keys into registers, and runs the same per-lane sampling and reduction code
 // as the single-scan kernel, writing each unit-split's FP64 partial sums into
 // that scan's slice of the batch's partial buffer.
-// Two sample groups in flight per lane keep every batched body within 64
-// registers; the order of the compensated additions is the same as with the
-// single-scan kernel's four, so results stay bit-identical to solo runs.
+// Fewer sample groups in flight per lane (two for N = 4, 8; one block of
+// three-call groups for N = 3, 6) keep the batched bodies near 64 registers;
+// the order of the compensated additions does not depend on the blocking, so
+// results stay bit-identical to solo runs.
 #ifndef ZMC_PAIR_GROUPS
 #define ZMC_PAIR_GROUPS 2
+#endif
+#ifndef ZMC_EVEN_GROUPS_C3
+#define ZMC_EVEN_GROUPS_C3 1
 #endif
 #include "zmc_scan_kernel.cuh"
 

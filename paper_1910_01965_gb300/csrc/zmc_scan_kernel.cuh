@@ -44,6 +44,9 @@ enum { kPrecFP64 = ZMC_FP64, kPrecFP32 = ZMC_FP32, kPrecFP32K = ZMC_FP32_KAHAN }
 #ifndef ZMC_EVEN_GROUPS
 #define ZMC_EVEN_GROUPS 4    // groups per block when G is even and a group is one call
 #endif
+#ifndef ZMC_EVEN_GROUPS_C3
+#define ZMC_EVEN_GROUPS_C3 2 // groups per block when G is even and a group is 3 calls
+#endif
 
 template <int PREC>
 struct LaneAcc;
@@ -247,7 +250,7 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
   if constexpr (ZMC_KAHAN_PAIRS && G % 2 == 0) {
     // Pairs within each group.  With one call per group (N = 1, 2) a block
     // of U groups puts U independent Philox chains in flight per lane.
-    constexpr int U = C == 1 ? ZMC_EVEN_GROUPS : 1;
+    constexpr int U = C == 1 ? ZMC_EVEN_GROUPS : (C <= 3 ? ZMC_EVEN_GROUPS_C3 : 1);
     auto consume = [&](const auto& r) {
       constexpr int V = sizeof(r) / sizeof(r[0]);
 #pragma unroll

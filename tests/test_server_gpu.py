@@ -136,6 +136,33 @@ def test_many_chunks_of_two_grids_interleaved(z):
         srv.close()
 
 
+def test_large_serving_request_full_size(z):
+    # The serving workload's large request at its full size (cos-product, N = 3,
+    # 465 x 465 x 463 > 10^8 points, 2^12 samples x 4 trials), streamed in
+    # chunks by the server: sampled points against the oracle, and every
+    # output against the same scan run alone.
+    spec = wl.large_scan(0)
+    srv = z.Server(60 << 30)
+    try:
+        t = srv.submit(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
+                       spec.samples, spec.trials, spec.seed)
+        assert srv.wait(t, 600000) == z.ZMC_OK
+        res, o = srv.result(t)
+        assert srv.stats().steps > 10
+        pts = wl.sample_points(spec.P, 200, seed=31)
+        ref = oracle.default().scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi,
+                                           spec.lengths, spec.values, spec.samples,
+                                           spec.trials, spec.seed, pts, want_sums=True)
+        got = {k: res[k][pts] for k in ("mean", "err", "errw")}
+        V = float(np.prod(spec.hi - spec.lo))
+        parity.check(got, ref, V, spec.samples, 2, spec.name + " served, sampled")
+        solo = _solo(z, spec, 2, o)
+        assert np.array_equal(res["mean"], solo["mean"])
+        assert np.array_equal(res["err"], solo["err"])
+    finally:
+        srv.close()
+
+
 def test_cancel_and_timeouts(z):
     srv = z.Server(1 << 30, step_ms=1.0, max_active=4)
     big = wl.scan_gauss_1e6(samples=1 << 14)  # ~0.2 s of GPU work
