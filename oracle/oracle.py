@@ -70,6 +70,9 @@ class Oracle:
         lib.zmc_oracle_word.argtypes = [ctypes.c_uint64, ctypes.c_int64,
                                         ctypes.c_int, ctypes.c_uint64]
         lib.zmc_oracle_word.restype = ctypes.c_uint32
+        lib.zmc_oracle_field.argtypes = [ctypes.c_uint64, ctypes.c_int64,
+                                         ctypes.c_int, ctypes.c_uint64]
+        lib.zmc_oracle_field.restype = ctypes.c_uint32
         lib.zmc_oracle_sample_y.argtypes = [ctypes.c_int, dp, dp,
                                             ctypes.c_uint64, ctypes.c_int64,
                                             ctypes.c_int, ctypes.c_int64, dp]
@@ -104,11 +107,17 @@ class Oracle:
         self.lib.zmc_oracle_philox4x32_10(c, k, o)
         return [int(v) for v in o]
 
-    def uniform(self, r: int) -> float:
-        return self.lib.zmc_oracle_uniform(int(r) & 0xFFFFFFFF)
+    def uniform(self, v: int) -> float:
+        """u = (2 v + 1) 2^-24 for a 23-bit field value v."""
+        return self.lib.zmc_oracle_uniform(int(v) & 0xFFFFFFFF)
 
     def word(self, seed: int, p: int, t: int, w: int) -> int:
+        """Raw word w of the Philox stream of (seed, p, t)."""
         return int(self.lib.zmc_oracle_word(seed, p, t, w))
+
+    def field(self, seed: int, p: int, t: int, i: int) -> int:
+        """23-bit field i of the stream of (seed, p, t)."""
+        return int(self.lib.zmc_oracle_field(seed, p, t, i))
 
     def sample_y(self, N, lo, hi, seed, p, t, s):
         lo = np.ascontiguousarray(lo, dtype=np.float64)

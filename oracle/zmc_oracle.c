@@ -16,11 +16,13 @@
  *
  * The paper names no random number generator.  This oracle draws samples
  * from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
- * as easy as 1, 2, 3", SC'11) with this counter layout: sample s, dimension k
- * of grid point p in trial t uses the 32-bit word w = s*N + k, which is lane
- * (w mod 4) of the Philox call with counter (floor(w/4), t, p mod 2^32,
- * p >> 32) and key (seed mod 2^32, seed >> 32).  The word r maps to
- * u = (2*(r >> 9) + 1) * 2^-24, strictly inside (0, 1), and to
+ * as easy as 1, 2, 3", SC'11).  Call j of grid point p in trial t has counter
+ * (j, t, p mod 2^32, p >> 32) and key (seed mod 2^32, seed >> 32); its four
+ * output words r0..r3 form the 128-bit block B = r0 + r1 2^32 + r2 2^64 +
+ * r3 2^96, which is cut into five 23-bit fields (bits 23m .. 23m+22 for
+ * m = 0..4; the top 13 bits are not used).  Field i of the stream is field
+ * (i mod 5) of call floor(i/5).  Sample s, dimension k uses field i = s*N + k:
+ * its value v maps to u = (2 v + 1) * 2^-24, strictly inside (0, 1), and to
  * y_k = fma(b_k - a_k, u, a_k).
  *
  * The estimator is written out plainly, in FP64, in sequential order:
@@ -76,23 +78,43 @@ void zmc_oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* The 32-bit word r -> u = (2*(r>>9)+1) * 2^-24, exactly, in (0, 1). */
-double zmc_oracle_uniform(uint32_t r) {
-  uint32_t odd = 2u * (r >> 9) + 1u;
+/* A 23-bit field value v (0 <= v < 2^23) -> u = (2 v + 1) * 2^-24, exactly,
+ * in (0, 1). */
+double zmc_oracle_uniform(uint32_t v) {
+  uint32_t odd = 2u * v + 1u;
   return ldexp((double)odd, -24);
 }
 
-/* Random word for (seed, p, t, w): lane w mod 4 of call floor(w/4). */
-uint32_t zmc_oracle_word(uint64_t seed, int64_t p, int t, uint64_t w) {
-  uint32_t ctr[4], key[2], out[4];
-  ctr[0] = (uint32_t)(w >> 2);
+/* The four output words of call j for (seed, p, t). */
+static void oracle_call(uint64_t seed, int64_t p, int t, uint64_t j, uint32_t out[4]) {
+  uint32_t ctr[4], key[2];
+  ctr[0] = (uint32_t)j;
   ctr[1] = (uint32_t)t;
   ctr[2] = (uint32_t)((uint64_t)p & 0xffffffffu);
   ctr[3] = (uint32_t)((uint64_t)p >> 32);
   key[0] = (uint32_t)(seed & 0xffffffffu);
   key[1] = (uint32_t)(seed >> 32);
   zmc_oracle_philox4x32_10(ctr, key, out);
+}
+
+/* Raw word w of the stream of (seed, p, t): lane w mod 4 of call floor(w/4). */
+uint32_t zmc_oracle_word(uint64_t seed, int64_t p, int t, uint64_t w) {
+  uint32_t out[4];
+  oracle_call(seed, p, t, w >> 2, out);
   return out[w & 3u];
+}
+
+/* Field i of the stream of (seed, p, t): bits 23m .. 23m+22 of the 128-bit
+ * block of call floor(i/5), m = i mod 5. */
+uint32_t zmc_oracle_field(uint64_t seed, int64_t p, int t, uint64_t i) {
+  uint32_t out[4];
+  uint64_t j = i / 5u;
+  int m = (int)(i % 5u);
+  oracle_call(seed, p, t, j, out);
+  int bit = 23 * m;
+  int q = bit / 32, sh = bit % 32;
+  uint64_t pair = (uint64_t)out[q] | ((uint64_t)out[q + 1] << 32);  /* q <= 2 */
+  return (uint32_t)((pair >> sh) & 0x7fffffu);
 }
 
 /* Sample point y (N values) for sample s of (p, t): direct MC over the box. */
@@ -100,8 +122,8 @@ void zmc_oracle_sample_y(int N, const double* lo, const double* hi,
                          uint64_t seed, int64_t p, int t, int64_t s,
                          double* y) {
   for (int k = 0; k < N; ++k) {
-    uint64_t w = (uint64_t)s * (uint64_t)N + (uint64_t)k;
-    double u = zmc_oracle_uniform(zmc_oracle_word(seed, p, t, w));
+    uint64_t i = (uint64_t)s * (uint64_t)N + (uint64_t)k;
+    double u = zmc_oracle_uniform(zmc_oracle_field(seed, p, t, i));
     y[k] = fma(hi[k] - lo[k], u, lo[k]);
   }
 }

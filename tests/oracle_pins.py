@@ -2,8 +2,9 @@
 
 Each ``pin_*`` function takes an ``oracle.Oracle`` (a loaded build) and raises
 AssertionError when the build disagrees with an outside fact:
-  - Philox4x32-10 and the counter layout: Triton's own Philox (a third-party
-    implementation, run in its CPU interpreter);
+  - Philox4x32-10, the counter layout and the cut of each call's 128 output
+    bits into five 23-bit fields: Triton's own Philox (a third-party
+    implementation, run in its CPU interpreter) and Python integers;
   - the uniform map and the map into the box: exact rational arithmetic;
   - grid decode (Sec. 2, C order): numpy's unravel_index / meshgrid('ij');
   - the estimator: closed forms of f(x) and of the variance of g (the sine-sum
@@ -52,6 +53,13 @@ def philox_requests():
     for (s, p, t, w) in layout:
         ctr.append([w >> 2, t, p & MASK32, p >> 32])
         seed.append(s)
+        # the same index read as a field index, and the fields of a 3-D sample
+        for i in [w] + [(w // 3) * 3 + k for k in range(3)]:
+            ctr.append([i // 5, t, p & MASK32, p >> 32])
+            seed.append(s)
+    for j in range(3):  # all slots of three consecutive calls
+        ctr.append([j, 2, 3, 0])
+        seed.append(7)
     return ctr, seed, layout
 
 
@@ -87,7 +95,7 @@ def reference_tables():
     for (gid, N, lo, hi, L, vals, S, T, sd, pts) in brute_cases():
         for p in pts:
             for t in range(T):
-                for j in range((S * N + 3) // 4):
+                for j in range((S * N + 4) // 5):
                     brute_keys.append((sd, p, t, j))
     for (sd, p, t, j) in brute_keys:
         ctr.append([j, t, p & MASK32, p >> 32])
@@ -101,6 +109,14 @@ def reference_tables():
 
 def _ref_word(ref, seed, p, t, w):
     return ref["table"][((w >> 2, t, p & MASK32, p >> 32), seed)][w & 3]
+
+
+def _ref_field(ref, seed, p, t, i):
+    """Field i: bits 23m..23m+22 (m = i mod 5) of call i // 5's four words
+    read as one 128-bit integer, lowest word first."""
+    r = ref["table"][((i // 5, t, p & MASK32, p >> 32), seed)]
+    block = r[0] | (r[1] << 32) | (r[2] << 64) | (r[3] << 96)
+    return (block >> (23 * (i % 5))) & (2 ** 23 - 1)
 
 
 # ---------------------------------------------------------------------------
@@ -120,20 +136,35 @@ def pin_word_layout(O, ref):
         assert O.word(s, p, t, w) == _ref_word(ref, s, p, t, w), (s, p, t, w)
 
 
+def pin_field_layout(O, ref):
+    for (s, p, t, w) in ref["layout"]:
+        assert O.field(s, p, t, w) == _ref_field(ref, s, p, t, w), (s, p, t, w)
+    # every slot of one call, and the two calls around a call boundary
+    s, p, t = 7, 3, 2
+    seen = set()
+    for i in range(15):
+        v = O.field(s, p, t, i)
+        assert 0 <= v < 2 ** 23
+        seen.add(v)
+        assert v == _ref_field(ref, s, p, t, i), i
+    assert len(seen) == 15
+
+
 def pin_uniform(O):
     rng = np.random.default_rng(1)
-    rs = [0, 1, 511, 512, 513, 2 ** 31, 2 ** 32 - 512, 2 ** 32 - 1] + \
-        [int(v) for v in rng.integers(0, 2 ** 32, 200, dtype=np.uint64)]
-    for r in rs:
-        u = O.uniform(r)
-        exact = Fraction(2 * (r >> 9) + 1, 2 ** 24)
-        assert Fraction(u) == exact, (r, u)
+    vs = [0, 1, 2, 2 ** 22 - 1, 2 ** 22, 2 ** 23 - 2, 2 ** 23 - 1] + \
+        [int(v) for v in rng.integers(0, 2 ** 23, 200)]
+    for v in vs:
+        u = O.uniform(v)
+        exact = Fraction(2 * v + 1, 2 ** 24)
+        assert Fraction(u) == exact, (v, u)
         assert 0.0 < u < 1.0
         assert float(np.float32(u)) == u  # exactly representable in FP32
 
 
 def pin_sample_y(O, ref):
-    # y_k = lo_k + (hi_k - lo_k) * u, rounded once (the box map of direct MC)
+    # y_k = lo_k + (hi_k - lo_k) * u, rounded once (the box map of direct MC),
+    # u from field s*N + k
     lo = [0.0, -0.5, -3.0]
     hi = [1.0, 1.5, 7.25]
     for (s, p, t, w) in ref["layout"][:12]:
@@ -141,8 +172,8 @@ def pin_sample_y(O, ref):
         samp = w // N
         y = O.sample_y(N, lo, hi, s, p, t, samp)
         for k in range(N):
-            r = O.word(s, p, t, samp * N + k)
-            u = Fraction(2 * (r >> 9) + 1, 2 ** 24)
+            v = _ref_field(ref, s, p, t, samp * N + k)
+            u = Fraction(2 * v + 1, 2 ** 24)
             wdt = Fraction(hi[k] - lo[k])  # the width as a double
             want = float(Fraction(lo[k]) + wdt * u)
             assert y[k] == want, (s, p, t, samp, k, y[k], want)
@@ -298,8 +329,8 @@ def pin_bruteforce(O, ref):
                 for s in range(S):
                     y = np.empty(N)
                     for k in range(N):
-                        r = _ref_word(ref, seed, p, t, s * N + k)
-                        u = Fraction(2 * (r >> 9) + 1, 2 ** 24)
+                        v = _ref_field(ref, seed, p, t, s * N + k)
+                        u = Fraction(2 * v + 1, 2 ** 24)
                         y[k] = float(Fraction(lo[k]) + Fraction(hi[k] - lo[k]) * u)
                     g.append(_numpy_g(gid, y, x))
                 g = np.array(g)
@@ -337,6 +368,7 @@ def all_pins(O, ref, fast=False):
     """Run every pin (used by the mutant test)."""
     pin_philox(O, ref)
     pin_word_layout(O, ref)
+    pin_field_layout(O, ref)
     pin_uniform(O)
     pin_sample_y(O, ref)
     pin_decode(O)

@@ -18,14 +18,20 @@ MUTANTS = [
     ("philox key bump", "if (round > 0) {", "if (round > 1) {"),
     ("philox rounds", "round < 10; ++round", "round < 9; ++round"),
     ("philox output order", "out[0] = c0; out[1] = c1;", "out[0] = c1; out[1] = c0;"),
-    ("uniform odd term", "uint32_t odd = 2u * (r >> 9) + 1u;", "uint32_t odd = 2u * (r >> 9);"),
-    ("uniform shift", "uint32_t odd = 2u * (r >> 9) + 1u;", "uint32_t odd = 2u * (r >> 8) + 1u;"),
-    ("call index", "ctr[0] = (uint32_t)(w >> 2);", "ctr[0] = (uint32_t)(w >> 1);"),
+    ("uniform odd term", "uint32_t odd = 2u * v + 1u;", "uint32_t odd = 2u * v;"),
+    ("uniform scale", "return ldexp((double)odd, -24);", "return ldexp((double)odd, -23);"),
+    ("word call index", "oracle_call(seed, p, t, w >> 2, out);", "oracle_call(seed, p, t, w >> 1, out);"),
+    ("field call index", "uint64_t j = i / 5u;", "uint64_t j = i / 4u;"),
+    ("field slot", "int m = (int)(i % 5u);", "int m = (int)(i % 4u);"),
+    ("field width", "int bit = 23 * m;", "int bit = 24 * m;"),
+    ("field mask", "return (uint32_t)((pair >> sh) & 0x7fffffu);", "return (uint32_t)((pair >> sh) & 0x3fffffu);"),
+    ("field word order", "uint64_t pair = (uint64_t)out[q] | ((uint64_t)out[q + 1] << 32);",
+     "uint64_t pair = (uint64_t)out[q + 1] | ((uint64_t)out[q] << 32);"),
     ("trial word", "ctr[1] = (uint32_t)t;", "ctr[1] = (uint32_t)(t + 1);"),
     ("point high word", "ctr[3] = (uint32_t)((uint64_t)p >> 32);", "ctr[3] = 0u;"),
     ("lane of the call", "return out[w & 3u];", "return out[(w + 1) & 3u];"),
-    ("word of a sample", "uint64_t w = (uint64_t)s * (uint64_t)N + (uint64_t)k;",
-     "uint64_t w = (uint64_t)s * 4u + (uint64_t)k;"),
+    ("field of a sample", "uint64_t i = (uint64_t)s * (uint64_t)N + (uint64_t)k;",
+     "uint64_t i = (uint64_t)s * 4u + (uint64_t)k;"),
     ("box base", "y[k] = fma(hi[k] - lo[k], u, lo[k]);", "y[k] = fma(hi[k] - lo[k], u, hi[k]);"),
     ("box width", "y[k] = fma(hi[k] - lo[k], u, lo[k]);", "y[k] = fma(hi[k], u, lo[k]);"),
     ("decode order", "for (int i = M - 1; i >= 0; --i) {", "for (int i = 0; i < M; ++i) {"),

@@ -18,6 +18,10 @@ def test_counter_layout_matches_triton(oracle_lib, philox_ref):
     op.pin_word_layout(oracle_lib, philox_ref)
 
 
+def test_field_layout_matches_triton(oracle_lib, philox_ref):
+    op.pin_field_layout(oracle_lib, philox_ref)
+
+
 def test_uniform_map_exact(oracle_lib):
     op.pin_uniform(oracle_lib)
 
