@@ -32,8 +32,8 @@ METRIC = ("MC evals/s on 1 GB300 and % FP32/SFU peak vs FP64 path; "
 # Algorithmic operations per integrand evaluation, from the method's steps
 # (counted per sample of N dimensions; see the measurement section of the
 # design notes): Philox4x32-10 = 10 rounds x (2 wide multiplies + 2 three-input
-# XORs) per 4 words -> 10 N; word -> u and u -> y: 2 N; the integrand; the
-# lane accumulation of g and g^2.
+# XORs) = 40 per call, and a call gives five 23-bit fields -> 8 N; field -> u
+# and u -> y: 2 N; the integrand; the lane accumulation of g and g^2.
 INTEGRAND_OPS = {
     0: lambda N: 0,              # const (draws no samples)
     1: lambda N: 3 * N - 1,      # cos-product: x*y, cos, product
@@ -46,7 +46,7 @@ ACCUM_OPS = {0: 2, 1: 2, 2: 9}   # FP64, FP32: add + fma; Kahan: g^2 + 2 x 4
 
 
 def ops_per_eval(gid: int, N: int, prec: int) -> int:
-    rng = 0 if gid == 0 else 10 * N + 2 * N
+    rng = 0 if gid == 0 else 8 * N + 2 * N
     return rng + INTEGRAND_OPS[gid](N) + ACCUM_OPS[prec]
 
 

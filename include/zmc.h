@@ -15,11 +15,13 @@
  *  - Grid order is C order over the lists: the flat index p has the last list
  *    varying fastest, as numpy's indexing='ij'.  Output arrays hold one FP64
  *    value per grid point in that order.
- *  - Random numbers: sample s, dimension k of grid point p in trial t uses the
- *    32-bit word w = s*N + k, lane (w mod 4) of Philox4x32-10 (Salmon et al.,
- *    SC'11) with counter (floor(w/4), t, p mod 2^32, p >> 32) and key
- *    (seed mod 2^32, seed >> 32); the word r becomes
- *    u = (2*(r >> 9) + 1) * 2^-24 and y_k = a_k + (b_k - a_k) * u.  The
+ *  - Random numbers: call j of grid point p in trial t is Philox4x32-10
+ *    (Salmon et al., SC'11) with counter (j, t, p mod 2^32, p >> 32) and key
+ *    (seed mod 2^32, seed >> 32).  Its four output words r0..r3 form the
+ *    128-bit block r0 + r1 2^32 + r2 2^64 + r3 2^96, cut into five 23-bit
+ *    fields (bits 23m .. 23m+22, m = 0..4).  Sample s, dimension k uses field
+ *    i = s*N + k, i.e. field (i mod 5) of call floor(i/5); its value v
+ *    becomes u = (2 v + 1) * 2^-24 and y_k = a_k + (b_k - a_k) * u.  The
  *    stream depends only on (seed, p, t, s, k), so any slice of the grid
  *    reproduces the full-grid values bit for bit.
  *  - Estimates: I_t = V * sum_s g / S with V = prod_k (b_k - a_k);
@@ -232,10 +234,11 @@ int zmc_scan_ex(const zmc_scan_desc* d, zmc_scan_out* o);
 
 /*
  * Raw random words of one unit's stream: out[i] = word (first_word + i) of
- * grid point p, trial t, under `seed` (the layout at the top of this file).
- * Sample s, dimension k is word s*N + k.  out is HOST memory of nwords
- * entries; first_word + nwords <= 2^34, nwords <= 2^30.  Computed on the GPU
- * by the same Philox code the sampling kernels use.  Synchronous.
+ * grid point p, trial t, under `seed`, where word w is output word (w mod 4)
+ * of call floor(w/4) (the calls at the top of this file; the samples' 23-bit
+ * fields are cut from these words).  out is HOST memory of nwords entries;
+ * first_word + nwords <= 2^34, nwords <= 2^30.  Computed on the GPU by the
+ * same Philox code the sampling kernels use.  Synchronous.
  */
 int zmc_stream_words(uint64_t seed, int64_t p, int t, uint64_t first_word,
                      int64_t nwords, uint32_t* out);

@@ -10,15 +10,12 @@
 // keys into registers, and runs the same per-lane sampling and reduction code
 // as the single-scan kernel, writing each unit-split's FP64 partial sums into
 // that scan's slice of the batch's partial buffer.
-// Fewer sample groups in flight per lane (two for N = 4, 8; one block of
-// three-call groups for N = 3, 6) keep the batched bodies near 64 registers;
-// the order of the compensated additions does not depend on the blocking, so
-// results stay bit-identical to solo runs.
-#ifndef ZMC_PAIR_GROUPS
-#define ZMC_PAIR_GROUPS 2
-#endif
-#ifndef ZMC_EVEN_GROUPS_C3
-#define ZMC_EVEN_GROUPS_C3 1
+// Fewer Philox calls in flight per lane (two instead of four, where a group
+// is shorter than that) keep the batched bodies near 64 registers; the order
+// of the compensated additions does not depend on the blocking, so results
+// stay bit-identical to solo runs.
+#ifndef ZMC_CALLS_IN_FLIGHT
+#define ZMC_CALLS_IN_FLIGHT 2
 #endif
 #include "zmc_scan_kernel.cuh"
 
@@ -34,13 +31,13 @@ namespace zmc {
 #define ZMC_BF(name) name##32
 #endif
 
-// Resident blocks per SM the register allocation is held to: 4 x 256 threads
-// (64 registers) for the FP32 paths, 3 for FP64 (its math library needs more).
+// Resident blocks per SM the register allocation is held to: 3 x 256 threads
+// (85 registers) for the FP32 paths, 2 for FP64 (its math library needs more).
 #ifndef ZMC_BATCH_MIN_BLOCKS
 #if ZMC_INST_PREC == 0
-#define ZMC_BATCH_MIN_BLOCKS 3
+#define ZMC_BATCH_MIN_BLOCKS 2
 #else
-#define ZMC_BATCH_MIN_BLOCKS 4
+#define ZMC_BATCH_MIN_BLOCKS 3
 #endif
 #endif
 

@@ -1,19 +1,20 @@
 // zmc_integrands.cuh — the compiled-in integrand registry, as device functors.
 //
 // Each functor evaluates g(y; x) (Eq. 1, Sec. 2) at one sample, reading the
-// sample's N raw Philox words.  The map of a word r to the box coordinate is
-// u = (2 (r >> 9) + 1) 2^-24, y = a + (b - a) u.
+// sample's N unit values f_k = 1 + v_k 2^-23 in [1, 2), one per dimension,
+// where v_k is the sample's 23-bit random field for dimension k (five fields
+// per Philox call; field23 below).  The box coordinate is
+// u = f - (1 - 2^-24) = (2 v + 1) 2^-24, y = a + (b - a) u.
 //
 // Two families:
-//  * FP64 functors (suffix 64) evaluate y and g in FP64, with the affine
-//    steps folded into per-unit constants as below.
-//  * FP32 functors (suffix 32) build the float f = 1 + (r >> 9) 2^-23 from the
-//    word's bits, so u = f - (1 - 2^-24) and y = (b - a) f + A with
-//    A = a - (b - a)(1 - 2^-24).  Everything affine in y that depends only on
-//    (x, box) is folded, in FP64, into per-unit constants before the sample
-//    loop; each sample then costs one FFMA per dimension before the
-//    integrand's own arithmetic.  cos/sin use the SFU (MUFU) approximations,
-//    exp uses ex2.approx.
+//  * FP64 functors (suffix 64, unit_t double) evaluate y and g in FP64, with
+//    the affine steps folded into per-unit constants as below.
+//  * FP32 functors (suffix 32, unit_t float) take f as a float built from
+//    the field's bits, so y = (b - a) f + A with A = a - (b - a)(1 - 2^-24).
+//    Everything affine in y that depends only on (x, box) is folded, in
+//    FP64, into per-unit constants before the sample loop; each sample then
+//    costs one FFMA per dimension before the integrand's own arithmetic.
+//    cos/sin use the SFU (MUFU) approximations, exp uses ex2.approx.
 //
 // kFixedM > 0 marks a functor compiled for one number of parameters M (the
 // run-time-compiled user integrands); it receives parameter i by set_param.
@@ -39,19 +40,27 @@ constexpr double kGaussScale = 2.83107266762673;  // to double precision
 // two differ by at most one unit in the last place of the exponent.
 constexpr double kGaussInvTwoSigma2 = 5.555555555555555;
 
-__device__ __forceinline__ float unit_f12(uint32_t r) {
-  // 1 + (r>>9) 2^-23: one funnel shift of (0x7f : r) right by 9 places the
-  // exponent bits 0x7f << 23 = 0x3f800000 above the 23 high bits of r.
-  return __uint_as_float(__funnelshift_r(r, 0x7fu, 9));
+// Field m (0..4) of one Philox call's four words: bits 23m .. 23m+22 of the
+// 128-bit block r[0] + r[1] 2^32 + r[2] 2^64 + r[3] 2^96 (m is a constant
+// wherever this is inlined, so the branch folds).
+__device__ __forceinline__ uint32_t field23(const uint32_t* r, int m) {
+  const int b = 23 * m, q = b >> 5, sh = b & 31;
+  const uint32_t x = (sh + 23 <= 32) ? (r[q] >> sh) : __funnelshift_r(r[q], r[q + 1], sh);
+  return x & 0x7fffffu;
 }
 
-__device__ __forceinline__ double unit_u64(uint32_t r) {
-  // 1 + (r>>9) 2^-23 built from bits, minus (1 - 2^-24): exactly
-  // (2 (r>>9) + 1) 2^-24.
-  const double d = __longlong_as_double(
-      static_cast<long long>(0x3FF0000000000000ull |
-                             (static_cast<uint64_t>(r >> 9) << 29)));
-  return d - kOneMinusHalfUlp;
+// The unit value f = 1 + v 2^-23 of a 23-bit field v, built from bits (the
+// mask above and the exponent below merge into one logic operation).
+template <class T>
+__device__ __forceinline__ T field_unit(uint32_t v);
+template <>
+__device__ __forceinline__ float field_unit<float>(uint32_t v) {
+  return __uint_as_float(0x3f800000u | v);
+}
+template <>
+__device__ __forceinline__ double field_unit<double>(uint32_t v) {
+  return __longlong_as_double(
+      static_cast<long long>(0x3FF0000000000000ull | (static_cast<uint64_t>(v) << 29)));
 }
 
 __device__ __forceinline__ float ex2_approx(float v) {
@@ -62,15 +71,10 @@ __device__ __forceinline__ float ex2_approx(float v) {
 
 // ------------------------------------------------------------------ FP64 --
 // FP64 functors fold the affine steps in y into per-unit constants the same way
-// the FP32 ones do: f = 1 + (r >> 9) 2^-23 exactly (built from bits), y =
-// (b - a) f + A with A = a - (b - a)(1 - 2^-24), so each dimension costs one
-// DFMA before the integrand's own arithmetic.  The result differs from
-// forming u first by at most a unit in the last place of each coordinate.
-
-__device__ __forceinline__ double unit_f64(uint32_t r) {
-  return __longlong_as_double(static_cast<long long>(
-      0x3FF0000000000000ull | (static_cast<uint64_t>(r >> 9) << 29)));
-}
+// the FP32 ones do: y = (b - a) f + A with A = a - (b - a)(1 - 2^-24), so each
+// dimension costs one DFMA before the integrand's own arithmetic.  The result
+// differs from forming u first by at most a unit in the last place of each
+// coordinate.
 
 template <int N>
 struct Const64 {
@@ -78,9 +82,10 @@ struct Const64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = false;
   static constexpr int kFixedM = 0;
+  using unit_t = double;
   __device__ void add(double) {}
   __device__ void finish(const double*, const double*) {}
-  __device__ double eval(const uint32_t*) const { return 1.0; }
+  __device__ double eval(const double*) const { return 1.0; }
 };
 
 // cos(x y) = cos(B f + C), B = x (b - a), C = x A.
@@ -90,16 +95,17 @@ struct CosProd64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = double;
   double B[N], C[N];
   __device__ void set(int i, double xi, double ai, double bi) {
     const double w = bi - ai;
     B[i] = xi * w;
     C[i] = xi * (ai - w * kOneMinusHalfUlp);
   }
-  __device__ double eval(const uint32_t* r) const {
-    double g = cos(fma(B[0], unit_f64(r[0]), C[0]));
+  __device__ double eval(const double* f) const {
+    double g = cos(fma(B[0], f[0], C[0]));
 #pragma unroll
-    for (int k = 1; k < N; ++k) g *= cos(fma(B[k], unit_f64(r[k]), C[k]));
+    for (int k = 1; k < N; ++k) g *= cos(fma(B[k], f[k], C[k]));
     return g;
   }
 };
@@ -111,18 +117,19 @@ struct Gauss64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = double;
   double W[N], C[N];
   __device__ void set(int i, double xi, double ai, double bi) {
     const double w = bi - ai;
     W[i] = w;
     C[i] = (ai - w * kOneMinusHalfUlp) - xi;
   }
-  __device__ double eval(const uint32_t* r) const {
-    double d = fma(W[0], unit_f64(r[0]), C[0]);
+  __device__ double eval(const double* f) const {
+    double d = fma(W[0], f[0], C[0]);
     double q = d * d;
 #pragma unroll
     for (int k = 1; k < N; ++k) {
-      d = fma(W[k], unit_f64(r[k]), C[k]);
+      d = fma(W[k], f[k], C[k]);
       q = fma(d, d, q);
     }
     return exp(-q * kGaussInvTwoSigma2);
@@ -135,6 +142,7 @@ struct Poly64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = double;
   double W[N], A[N], X[N];
   __device__ void set(int i, double xi, double ai, double bi) {
     const double w = bi - ai;
@@ -142,12 +150,12 @@ struct Poly64 {
     A[i] = ai - w * kOneMinusHalfUlp;
     X[i] = xi;
   }
-  __device__ double eval(const uint32_t* r) const {
-    double y = fma(W[0], unit_f64(r[0]), A[0]);
+  __device__ double eval(const double* f) const {
+    double y = fma(W[0], f[0], A[0]);
     double g = fma(X[0] * y, y, 1.0);
 #pragma unroll
     for (int k = 1; k < N; ++k) {
-      y = fma(W[k], unit_f64(r[k]), A[k]);
+      y = fma(W[k], f[k], A[k]);
       g *= fma(X[k] * y, y, 1.0);
     }
     return g;
@@ -160,6 +168,7 @@ struct Osc64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = double;
   double W[N], A[N], X[N];
   __device__ void set(int i, double xi, double ai, double bi) {
     const double w = bi - ai;
@@ -167,11 +176,11 @@ struct Osc64 {
     A[i] = ai - w * kOneMinusHalfUlp;
     X[i] = xi;
   }
-  __device__ double eval(const uint32_t* r) const {
+  __device__ double eval(const double* f) const {
     double lin = 0.0, quad = 0.0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      const double y = fma(W[k], unit_f64(r[k]), A[k]);
+      const double y = fma(W[k], f[k], A[k]);
       lin = fma(X[k], y, lin);
       quad = fma(y, y, quad);
     }
@@ -186,6 +195,7 @@ struct SinSum64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = double;
   double xsum, W[N], C0;
   __device__ void add(double xi) { xsum += xi; }
   __device__ void finish(const double* lo, const double* hi) {
@@ -198,10 +208,10 @@ struct SinSum64 {
     }
     C0 = c;
   }
-  __device__ double eval(const uint32_t* r) const {
+  __device__ double eval(const double* f) const {
     double s = C0;
 #pragma unroll
-    for (int k = 0; k < N; ++k) s = fma(W[k], unit_f64(r[k]), s);
+    for (int k = 0; k < N; ++k) s = fma(W[k], f[k], s);
     return sin(s);
   }
 };
@@ -219,9 +229,10 @@ struct Const32 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = false;
   static constexpr int kFixedM = 0;
+  using unit_t = float;
   __device__ void add(double) {}
   __device__ void finish(const double*, const double*) {}
-  __device__ float eval(const uint32_t*) const { return 1.0f; }
+  __device__ float eval(const float*) const { return 1.0f; }
 };
 
 // cos(x y) = cos(B f + C), B = x (b - a), C = x A.
@@ -231,6 +242,7 @@ struct CosProd32 {
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = float;
   float B[N], C[N];
   static __device__ float2 value(int, double x, double a, double b) {
     const double w = b - a;
@@ -239,10 +251,10 @@ struct CosProd32 {
   }
   static __device__ void dim(int, double, double, float*) {}
   __device__ void load(int k, float2 v, const float*) { B[k] = v.x; C[k] = v.y; }
-  __device__ float eval(const uint32_t* r) const {
-    float g = __cosf(fmaf(B[0], unit_f12(r[0]), C[0]));
+  __device__ float eval(const float* f) const {
+    float g = __cosf(fmaf(B[0], f[0], C[0]));
 #pragma unroll
-    for (int k = 1; k < N; ++k) g *= __cosf(fmaf(B[k], unit_f12(r[k]), C[k]));
+    for (int k = 1; k < N; ++k) g *= __cosf(fmaf(B[k], f[k], C[k]));
     return g;
   }
 };
@@ -255,6 +267,7 @@ struct Gauss32 {
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = float;
   float B[N], C[N];
   static __device__ float2 value(int, double x, double a, double b) {
     const double w = b - a;
@@ -264,12 +277,12 @@ struct Gauss32 {
     out[0] = static_cast<float>((b - a) * kGaussScale);
   }
   __device__ void load(int k, float2 v, const float* d) { B[k] = d[0]; C[k] = v.x; }
-  __device__ float eval(const uint32_t* r) const {
-    float d = fmaf(B[0], unit_f12(r[0]), C[0]);
+  __device__ float eval(const float* f) const {
+    float d = fmaf(B[0], f[0], C[0]);
     float q = d * d;
 #pragma unroll
     for (int k = 1; k < N; ++k) {
-      d = fmaf(B[k], unit_f12(r[k]), C[k]);
+      d = fmaf(B[k], f[k], C[k]);
       q = fmaf(d, d, q);
     }
     return ex2_approx(-q);
@@ -283,6 +296,7 @@ struct Poly32 {
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = float;
   float W[N], A[N], X[N];
   static __device__ float2 value(int, double x, double, double) {
     return make_float2(static_cast<float>(x), 0.f);
@@ -293,12 +307,12 @@ struct Poly32 {
     out[1] = static_cast<float>(a - w * kOneMinusHalfUlp);
   }
   __device__ void load(int k, float2 v, const float* d) { W[k] = d[0]; A[k] = d[1]; X[k] = v.x; }
-  __device__ float eval(const uint32_t* r) const {
-    float y = fmaf(W[0], unit_f12(r[0]), A[0]);
+  __device__ float eval(const float* f) const {
+    float y = fmaf(W[0], f[0], A[0]);
     float g = fmaf(X[0] * y, y, 1.0f);
 #pragma unroll
     for (int k = 1; k < N; ++k) {
-      y = fmaf(W[k], unit_f12(r[k]), A[k]);
+      y = fmaf(W[k], f[k], A[k]);
       g *= fmaf(X[k] * y, y, 1.0f);
     }
     return g;
@@ -312,6 +326,7 @@ struct Osc32 {
   static constexpr bool kTable = true;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = float;
   float W[N], A[N], X[N];
   static __device__ float2 value(int, double x, double, double) {
     return make_float2(static_cast<float>(x), 0.f);
@@ -322,12 +337,12 @@ struct Osc32 {
     out[1] = static_cast<float>(a - w * kOneMinusHalfUlp);
   }
   __device__ void load(int k, float2 v, const float* d) { W[k] = d[0]; A[k] = d[1]; X[k] = v.x; }
-  __device__ float eval(const uint32_t* r) const {
-    float y = fmaf(W[0], unit_f12(r[0]), A[0]);
+  __device__ float eval(const float* f) const {
+    float y = fmaf(W[0], f[0], A[0]);
     float ph = y * fmaf(static_cast<float>(kOscQuad), y, X[0]);
 #pragma unroll
     for (int k = 1; k < N; ++k) {
-      y = fmaf(W[k], unit_f12(r[k]), A[k]);
+      y = fmaf(W[k], f[k], A[k]);
       ph = fmaf(y, fmaf(static_cast<float>(kOscQuad), y, X[k]), ph);
     }
     return __cosf(ph);
@@ -341,6 +356,7 @@ struct SinSum32 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = 0;
+  using unit_t = float;
   double xsum;
   float W[N], C0;
   __device__ void add(double xi) { xsum += xi; }
@@ -356,10 +372,10 @@ struct SinSum32 {
     c = c - two_pi * floor(c / two_pi);
     C0 = static_cast<float>(c);
   }
-  __device__ float eval(const uint32_t* r) const {
+  __device__ float eval(const float* f) const {
     float s = C0;
 #pragma unroll
-    for (int k = 0; k < N; ++k) s = fmaf(W[k], unit_f12(r[k]), s);
+    for (int k = 0; k < N; ++k) s = fmaf(W[k], f[k], s);
     return __sinf(s);
   }
 };

@@ -61,10 +61,12 @@ struct FinalizeArgs {
   double* s2;     // may be null, [count][T]
 };
 
-// Samples per group G and Philox calls per group C for dimension N:
-// G samples use exactly G*N = 4*C consecutive words.
-constexpr int group_samples(int N) { return (N % 4 == 0) ? 1 : (N % 2 == 0 ? 2 : 4); }
-constexpr int group_calls(int N) { return N * group_samples(N) / 4; }
+// Each Philox call gives five 23-bit fields.  Samples per group G and calls
+// per group C for dimension N (1..8): G samples use exactly G*N = 5*C
+// consecutive fields, so a group starts and ends on call boundaries.
+constexpr int kFieldsPerCall = 5;
+constexpr int group_samples(int N) { return (N % 5 == 0) ? 1 : 5; }
+constexpr int group_calls(int N) { return N * group_samples(N) / kFieldsPerCall; }
 
 // Launches of one precision's sampling kernel for (integrand, N).
 // Returns a CUDA error code (0 = success).

@@ -114,6 +114,14 @@ struct StridedProduct {
     mulhilo32(kPhiloxM0, stride, dhi, dlo);
   }
   __device__ __forceinline__ void advance() { add64(lo, hi, dlo, dhi); }
+  // M0 * (j + c) for a small constant c: M0 * j plus the constant M0 * c (a
+  // 64-bit add of an immediate), so the calls of one group share one product.
+  __device__ __forceinline__ void at(int c, uint32_t& H, uint32_t& L) const {
+    const uint64_t v = ((static_cast<uint64_t>(hi) << 32) | lo) +
+                       static_cast<uint64_t>(kPhiloxM0) * static_cast<uint64_t>(c);
+    L = static_cast<uint32_t>(v);
+    H = static_cast<uint32_t>(v >> 32);
+  }
 };
 
 }  // namespace zmc

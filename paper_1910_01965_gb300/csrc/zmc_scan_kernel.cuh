@@ -11,8 +11,8 @@
 // the statistics.
 //
 // Sample groups: G = group_samples(N) consecutive samples use exactly
-// C = group_calls(N) Philox calls (G*N = 4C words), so a lane always works on
-// whole groups and never shares a call with another lane.
+// C = group_calls(N) Philox calls (G*N = 5C fields), so a lane always works
+// on whole groups and never shares a call with another lane.
 #pragma once
 
 #include <cstdint>
@@ -32,20 +32,8 @@ enum { kPrecFP64 = ZMC_FP64, kPrecFP32 = ZMC_FP32, kPrecFP32K = ZMC_FP32_KAHAN }
 #ifndef ZMC_LB_MIN_BLOCKS
 #define ZMC_LB_MIN_BLOCKS 1  // __launch_bounds__ minimum resident blocks
 #endif
-#ifndef ZMC_UNROLL_SMALL
-#define ZMC_UNROLL_SMALL 2   // sample groups in flight per lane when C <= 2
-#endif
-#ifndef ZMC_KAHAN_PAIRS
-#define ZMC_KAHAN_PAIRS 1    // 1: compensated sums take pairs of samples
-#endif
-#ifndef ZMC_PAIR_GROUPS
-#define ZMC_PAIR_GROUPS 4    // groups in flight per lane when G == 1 (2 or 4)
-#endif
-#ifndef ZMC_EVEN_GROUPS
-#define ZMC_EVEN_GROUPS 4    // groups per block when G is even and a group is one call
-#endif
-#ifndef ZMC_EVEN_GROUPS_C3
-#define ZMC_EVEN_GROUPS_C3 2 // groups per block when G is even and a group is 3 calls
+#ifndef ZMC_CALLS_IN_FLIGHT
+#define ZMC_CALLS_IN_FLIGHT 4  // independent Philox calls per lane per loop block
 #endif
 
 template <int PREC>
@@ -212,13 +200,28 @@ __device__ __forceinline__ const void* stage_lists(const ScanArgs& a, double* sm
   }
 }
 
+// Sample g of a group whose C calls' words are r[0 .. 4C): its N unit values
+// come from the group's fields g*N .. g*N + N - 1 (field e is field e mod 5
+// of the group's call e / 5).
+template <int N, class F>
+__device__ __forceinline__ auto eval_sample(const F& f, const uint32_t* r, int g) {
+  typename F::unit_t u[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int e = g * N + k;
+    u[k] = field_unit<typename F::unit_t>(
+        field23(r + 4 * (e / kFieldsPerCall), e % kFieldsPerCall));
+  }
+  return f.eval(u);
+}
+
 // Sum over the sample groups [q, q_end) with stride `step` (one lane).
 //
 // Order of the compensated additions (the same for every blocking choice
-// below, so the single-scan and batched kernels agree bit for bit): with G
-// even, each group's samples enter as pairs (0,1), (2,3), ... in group order;
-// with G odd (G == 1), consecutive groups are paired and a last unpaired
-// group enters alone.
+// below, so the single-scan and batched kernels agree bit for bit): with
+// G = 5, each group's samples enter as pairs (0,1), (2,3) and then sample 4
+// alone, in group order; with G = 1, consecutive groups are paired and a last
+// unpaired group enters alone.
 template <int N, class F, int PREC>
 __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
                                             const uint32_t* __restrict__ rk1,
@@ -227,57 +230,89 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
                                             LaneAcc<PREC>& acc) {
   constexpr int G = group_samples(N);
   constexpr int C = group_calls(N);
-  // Two groups in flight give each lane two independent Philox chains; for
-  // C >= 3 one group already has C independent calls (and 2x the registers
-  // would spill).
-  constexpr int kUnroll = C <= 2 ? ZMC_UNROLL_SMALL : 1;
+  // Groups per loop block: about ZMC_CALLS_IN_FLIGHT independent Philox
+  // chains per lane (a group of C calls already has C).  The FP64 path is
+  // bound by its FP64 arithmetic, not by the stream: one group at a time.
+  constexpr int kCalls = PREC == kPrecFP64 ? 1 : ZMC_CALLS_IN_FLIGHT;
+  constexpr int kBlock = kCalls / C > 1 ? kCalls / C : 1;
   // M0 * j for the lane's calls, carried along by 64-bit adds: call c of
-  // group q has j = q C + c, and the lane's groups advance by `step`.
-  StridedProduct sp[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c) sp[c].init(q * C + c, step * C);
+  // group q has j = q C + c; the product for q C advances with the lane's
+  // stride and call c adds the constant M0 c to it.
+  StridedProduct sp;
+  sp.init(q * C, step * C);
+  auto call = [&](int c, uint32_t* out) {
+    uint32_t H, L;
+    sp.at(c, H, L);
+    philox_call_pre(pu, rk0, rk1, H, L, out);
+  };
   // Draw the words of V consecutive groups of this lane.
   auto draw = [&](auto& r) {
     constexpr int V = sizeof(r) / sizeof(r[0]);
 #pragma unroll
-    for (int u = 0; u < V; ++u)
+    for (int u = 0; u < V; ++u) {
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[u][4 * c]);
-        sp[c].advance();
-      }
+      for (int c = 0; c < C; ++c) call(c, &r[u][4 * c]);
+      sp.advance();
+    }
   };
-  if constexpr (ZMC_KAHAN_PAIRS && G % 2 == 0) {
-    // Pairs within each group.  With one call per group (N = 1, 2) a block
-    // of U groups puts U independent Philox chains in flight per lane.
-    constexpr int U = C == 1 ? ZMC_EVEN_GROUPS : (C <= 3 ? ZMC_EVEN_GROUPS_C3 : 1);
+  if constexpr (G > 1) {
+    constexpr int U = kBlock;
     auto consume = [&](const auto& r) {
       constexpr int V = sizeof(r) / sizeof(r[0]);
 #pragma unroll
-      for (int u = 0; u < V; ++u)
+      for (int u = 0; u < V; ++u) {
 #pragma unroll
-        for (int g = 0; g < G; g += 2)
-          acc.add2(f.eval(&r[u][g * N]), f.eval(&r[u][(g + 1) * N]));
+        for (int g = 0; g + 1 < G; g += 2)
+          acc.add2(eval_sample<N>(f, r[u], g), eval_sample<N>(f, r[u], g + 1));
+        if constexpr (G % 2 == 1) acc.add(eval_sample<N>(f, r[u], G - 1));
+      }
     };
-    for (; q + (U - 1) * step < q_end; q += U * step) {
-      uint32_t r[U][4 * C];
-      draw(r);
-      consume(r);
-    }
-    if constexpr (U > 1) {
+    if constexpr (U == 1 && C > 2) {
+      // One long group at a time: each call is drawn just before the first
+      // sample that reads it, so a call's words die once its last sample is
+      // evaluated (fewer live registers than drawing all C calls first).
       for (; q < q_end; q += step) {
-        uint32_t r[1][4 * C];
+        uint32_t r[4 * C];
+        float dummy = 0.0f;
+        auto prev = static_cast<typename F::unit_t>(dummy);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int c0 = g == 0 ? 0 : (g * N - 1) / kFieldsPerCall + 1;
+          const int c1 = (g * N + N - 1) / kFieldsPerCall;
+#pragma unroll
+          for (int c = c0; c <= c1; ++c) call(c, &r[4 * c]);
+          const auto v = eval_sample<N>(f, r, g);
+          if (g % 2 == 1)
+            acc.add2(prev, v);
+          else if (g == G - 1)
+            acc.add(v);
+          else
+            prev = v;
+        }
+        sp.advance();
+      }
+    } else {
+      for (; q + (U - 1) * step < q_end; q += U * step) {
+        uint32_t r[U][4 * C];
         draw(r);
         consume(r);
       }
+      if constexpr (U > 1) {
+        for (; q < q_end; q += step) {
+          uint32_t r[1][4 * C];
+          draw(r);
+          consume(r);
+        }
+      }
     }
-  } else if constexpr (ZMC_KAHAN_PAIRS && kUnroll % 2 == 0) {
+  } else {
     // G == 1: consecutive groups are paired; U groups (U/2 pairs) per block.
-    constexpr int U = ZMC_PAIR_GROUPS;
+    constexpr int U = kBlock >= 2 ? kBlock & ~1 : 2;
     auto consume = [&](const auto& r) {
       constexpr int V = sizeof(r) / sizeof(r[0]);
 #pragma unroll
-      for (int u = 0; u < V; u += 2) acc.add2(f.eval(&r[u][0]), f.eval(&r[u + 1][0]));
+      for (int u = 0; u < V; u += 2)
+        acc.add2(eval_sample<N>(f, r[u], 0), eval_sample<N>(f, r[u + 1], 0));
     };
     for (; q + (U - 1) * step < q_end; q += U * step) {
       uint32_t r[U][4 * C];
@@ -295,24 +330,13 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
     if (q < q_end) {
       uint32_t r[1][4 * C];
       draw(r);
-      acc.add(f.eval(&r[0][0]));
-    }
-  } else {
-#pragma unroll kUnroll
-    for (; q < q_end; q += step) {
-      uint32_t r[4 * C];
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        philox_call_pre(pu, rk0, rk1, sp[c].hi, sp[c].lo, &r[4 * c]);
-        sp[c].advance();
-      }
-#pragma unroll
-      for (int g = 0; g < G; ++g) acc.add(f.eval(&r[g * N]));
+      acc.add(eval_sample<N>(f, r[0], 0));
     }
   }
 }
 
-// The ragged last group of a unit when G does not divide S.
+// The ragged last group of a unit when G does not divide S: its valid samples
+// enter one at a time.
 template <int N, class F, int PREC>
 __device__ __forceinline__ void lane_tail_group(const uint32_t* __restrict__ rk0,
                                                 const uint32_t* __restrict__ rk1,
@@ -325,7 +349,7 @@ __device__ __forceinline__ void lane_tail_group(const uint32_t* __restrict__ rk0
   for (int c = 0; c < C; ++c) philox_call(pu, rk0, rk1, q * C + c, &r[4 * c]);
 #pragma unroll
   for (int g = 0; g < G; ++g)
-    if (g < valid) acc.add(f.eval(&r[g * N]));
+    if (g < valid) acc.add(eval_sample<N>(f, r, g));
 }
 
 // Work of one lane for unit-split `us`: decode, prepare, sample, sum.

@@ -2,9 +2,9 @@
 //
 // Included only by the translation unit that NVRTC compiles for a user
 // integrand (zmc_user.cu), after the user's source and with ZMC_N and ZMC_M
-// defined.  They map the sample's words to y exactly as the built-in
-// functors do (FP32: y = W f + A from the float 1 + (r >> 9) 2^-23; FP64:
-// y = fma(b - a, u, a)) and call the user's g.
+// defined.  They map the sample's unit values f = 1 + v 2^-23 to y exactly
+// as the built-in functors do (FP32: y = W f + A; FP64: y = fma(b - a, u, a)
+// with u = f - (1 - 2^-24)) and call the user's g.
 #pragma once
 
 #include "zmc_integrands.cuh"
@@ -17,6 +17,7 @@ struct UserF32 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = ZMC_M;
+  using unit_t = float;
   float W[N], A[N], X[ZMC_M];
   __device__ void set_param(int i, double xi) { X[i] = static_cast<float>(xi); }
   __device__ void add(double) {}
@@ -28,10 +29,10 @@ struct UserF32 {
       A[k] = static_cast<float>(lo[k] - w * kOneMinusHalfUlp);
     }
   }
-  __device__ float eval(const uint32_t* r) const {
+  __device__ float eval(const float* f) const {
     float y[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) y[k] = fmaf(W[k], unit_f12(r[k]), A[k]);
+    for (int k = 0; k < N; ++k) y[k] = fmaf(W[k], f[k], A[k]);
     return zmc_user_g32(y, X);
   }
 };
@@ -42,6 +43,7 @@ struct UserF64 {
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
   static constexpr int kFixedM = ZMC_M;
+  using unit_t = double;
   double w[N], a[N], X[ZMC_M];
   __device__ void set_param(int i, double xi) { X[i] = xi; }
   __device__ void add(double) {}
@@ -52,10 +54,10 @@ struct UserF64 {
       w[k] = hi[k] - lo[k];
     }
   }
-  __device__ double eval(const uint32_t* r) const {
+  __device__ double eval(const double* f) const {
     double y[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) y[k] = fma(w[k], unit_u64(r[k]), a[k]);
+    for (int k = 0; k < N; ++k) y[k] = fma(w[k], f[k] - kOneMinusHalfUlp, a[k]);
     return zmc_user_g64(y, X);
   }
 };
