@@ -10,13 +10,9 @@
 // keys into registers, and runs the same per-lane sampling and reduction code
 // as the single-scan kernel, writing each unit-split's FP64 partial sums into
 // that scan's slice of the batch's partial buffer.
-// Fewer Philox calls in flight per lane (two instead of four, where a group
-// is shorter than that) keep the batched bodies near 64 registers; the order
-// of the compensated additions does not depend on the blocking, so results
-// stay bit-identical to solo runs.
-#ifndef ZMC_CALLS_IN_FLIGHT
-#define ZMC_CALLS_IN_FLIGHT 2
-#endif
+// The batched bodies keep as many Philox calls in flight per lane as the
+// single-scan kernel; the order of the compensated additions does not depend
+// on the blocking in any case, so results stay bit-identical to solo runs.
 #include "zmc_scan_kernel.cuh"
 
 #ifndef ZMC_INST_PREC
@@ -31,14 +27,11 @@ namespace zmc {
 #define ZMC_BF(name) name##32
 #endif
 
-// Resident blocks per SM the register allocation is held to: 3 x 256 threads
-// (85 registers) for the FP32 paths, 2 for FP64 (its math library needs more).
+// Resident blocks per SM the register allocation is held to: 2 x 256 threads
+// (128 registers), so that the FP32 bodies do not spill; the largest bodies
+// set the residency of the whole launch (measured: faster than 85 or 64).
 #ifndef ZMC_BATCH_MIN_BLOCKS
-#if ZMC_INST_PREC == 0
 #define ZMC_BATCH_MIN_BLOCKS 2
-#else
-#define ZMC_BATCH_MIN_BLOCKS 3
-#endif
 #endif
 
 // One tile.  Not inlined: each (integrand, N) body gets its own register

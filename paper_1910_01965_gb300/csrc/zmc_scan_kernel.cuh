@@ -50,6 +50,11 @@ struct LaneAcc<kPrecFP64> {
     add(a);
     add(b);
   }
+  template <int K>
+  __device__ __forceinline__ void add_group(const double* v) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) add(v[i]);
+  }
   __device__ __forceinline__ double sum1() const { return s1; }
   __device__ __forceinline__ double sum2() const { return s2; }
 };
@@ -64,6 +69,11 @@ struct LaneAcc<kPrecFP32> {
   __device__ __forceinline__ void add2(float a, float b) {
     add(a);
     add(b);
+  }
+  template <int K>
+  __device__ __forceinline__ void add_group(const float* v) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) add(v[i]);
   }
   __device__ __forceinline__ double sum1() const { return s1; }
   __device__ __forceinline__ double sum2() const { return s2; }
@@ -95,6 +105,25 @@ struct LaneAcc<kPrecFP32K> {
     c1 = (t1 - s1) - y1;
     s1 = t1;
     const float y2 = v - c2;
+    const float t2 = s2 + y2;
+    c2 = (t2 - s2) - y2;
+    s2 = t2;
+  }
+  // K samples at once (a sample group): their plain FP32 sums, formed in a
+  // fixed order, enter the compensated sums in one step.
+  template <int K>
+  __device__ __forceinline__ void add_group(const float* v) {
+    float u = v[0], w = v[0] * v[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i) {
+      u += v[i];
+      w = fmaf(v[i], v[i], w);
+    }
+    const float y1 = u - c1;
+    const float t1 = s1 + y1;
+    c1 = (t1 - s1) - y1;
+    s1 = t1;
+    const float y2 = w - c2;
     const float t2 = s2 + y2;
     c2 = (t2 - s2) - y2;
     s2 = t2;
@@ -219,9 +248,9 @@ __device__ __forceinline__ auto eval_sample(const F& f, const uint32_t* r, int g
 //
 // Order of the compensated additions (the same for every blocking choice
 // below, so the single-scan and batched kernels agree bit for bit): with
-// G = 5, each group's samples enter as pairs (0,1), (2,3) and then sample 4
-// alone, in group order; with G = 1, consecutive groups are paired and a last
-// unpaired group enters alone.
+// G = 5, each group's five samples enter in one step (LaneAcc::add_group), in
+// group order; with G = 1, consecutive groups are paired and a last unpaired
+// group enters alone.
 template <int N, class F, int PREC>
 __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
                                             const uint32_t* __restrict__ rk1,
@@ -257,14 +286,15 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
   };
   if constexpr (G > 1) {
     constexpr int U = kBlock;
+    using T = typename F::unit_t;
     auto consume = [&](const auto& r) {
       constexpr int V = sizeof(r) / sizeof(r[0]);
 #pragma unroll
       for (int u = 0; u < V; ++u) {
+        T v[G];
 #pragma unroll
-        for (int g = 0; g + 1 < G; g += 2)
-          acc.add2(eval_sample<N>(f, r[u], g), eval_sample<N>(f, r[u], g + 1));
-        if constexpr (G % 2 == 1) acc.add(eval_sample<N>(f, r[u], G - 1));
+        for (int g = 0; g < G; ++g) v[g] = eval_sample<N>(f, r[u], g);
+        acc.template add_group<G>(v);
       }
     };
     if constexpr (U == 1 && C > 2) {
@@ -273,22 +303,16 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
       // evaluated (fewer live registers than drawing all C calls first).
       for (; q < q_end; q += step) {
         uint32_t r[4 * C];
-        float dummy = 0.0f;
-        auto prev = static_cast<typename F::unit_t>(dummy);
+        T v[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
           const int c0 = g == 0 ? 0 : (g * N - 1) / kFieldsPerCall + 1;
           const int c1 = (g * N + N - 1) / kFieldsPerCall;
 #pragma unroll
           for (int c = c0; c <= c1; ++c) call(c, &r[4 * c]);
-          const auto v = eval_sample<N>(f, r, g);
-          if (g % 2 == 1)
-            acc.add2(prev, v);
-          else if (g == G - 1)
-            acc.add(v);
-          else
-            prev = v;
+          v[g] = eval_sample<N>(f, r, g);
         }
+        acc.template add_group<G>(v);
         sp.advance();
       }
     } else {
