@@ -160,6 +160,26 @@ def test_edge_cases(zmc):
         parity.check(got, _oracle(spec), 1.0, spec.samples, prec, "long list")
 
 
+@pytest.mark.parametrize("N", [1, 2, 4, 5, 7])
+def test_every_small_sample_count(zmc, N):
+    # S = 1 .. 12 covers samples fewer than one group, exactly one group, a
+    # group plus a ragged tail and (N = 5) single-sample groups; the sums must
+    # match the oracle's, and the tile shape (one lane or 32 lanes, one or
+    # several sample ranges) must not matter beyond summation order.
+    lists = [np.linspace(0.5, 5.0, 3 + k) for k in range(min(N, 3))] + [[1.0]] * max(0, N - 3)
+    for S in range(1, 13):
+        spec = wl.ScanSpec("S%d" % S, wl.G_COSPROD, N, np.zeros(N), np.ones(N), lists, S, 3, S)
+        ref = _oracle(spec)
+        for prec in PRECS:
+            for tiles in [(0, 0, 0), (1, 1, 64), (32, 2, 128)]:
+                got, _ = _gpu(zmc, spec, prec, tiles=tiles)
+                V = _V(spec)
+                scale = V * np.maximum(1.0, np.sqrt(np.mean(ref["s2"], axis=1) / S))
+                tol = (1e-12 if prec == 0 else 1e-5) * scale
+                assert np.all(np.abs(got["mean"] - ref["mean"]) <= tol), (N, S, prec, tiles)
+                assert np.allclose(got["s1"], ref["s1"], rtol=0, atol=(1e-12 if prec == 0 else 1e-5) * S)
+
+
 def test_grid_index_beyond_32_bits(zmc):
     big = 70000  # P = 4.9e9 > 2^32: the high counter word of p is non-zero
     spec = wl.ScanSpec("big", wl.G_GAUSS03, 2, -np.ones(2), np.ones(2),
