@@ -373,6 +373,87 @@ def run_serving_sweep(args, world, rank, local):
     return 0
 
 
+def small_scan_batch(zmc, torch, prec, stream):
+    """2048 small scans of the serving mix's kind (the uneven generator with
+    samples capped at 2^11 and lists at 8 values): descriptors, outputs and
+    the buffers they point into."""
+    from paper_1910_01965_gb300 import workloads as wl
+    small = [s for s in wl.batch_uneven_256(count=2048, seed=7)]
+    for s_ in small:
+        s_.samples = int(min(s_.samples, 1 << 11))
+        s_.lists = [v[:min(len(v), 8)] for v in s_.lists]
+    sd, so, sk = [], [], []
+    for sp in small:
+        vals = torch.tensor(sp.values, dtype=torch.float64, device="cuda")
+        d, k = zmc.make_desc(sp.integrand_id, sp.N, sp.lo, sp.hi, sp.lengths, vals, sp.samples,
+                             sp.trials, sp.seed, prec, mem=zmc.ZMC_MEM_DEVICE)
+        d.stream = stream.cuda_stream
+        m = torch.empty(sp.P, dtype=torch.float64, device="cuda")
+        e = torch.empty_like(m)
+        o = zmc.zmc_scan_out()
+        o.mean, o.err = zmc._ptr(m), zmc._ptr(e)
+        sd.append(d)
+        so.append(o)
+        sk.append((k, vals, m, e))
+    return small, sd, so, sk
+
+
+def run_small_batch_bench(args, world, rank, local):
+    """One step = one graph replay of 2048 small scans in one persistent launch
+    per precision (the serving mix's typical requests)."""
+    import torch
+    from paper_1910_01965_gb300 import zmc
+    torch.cuda.set_device(local)
+    zmc.load()
+    prec = zmc.PRECISIONS[args.precision]
+    stream = torch.cuda.current_stream()
+    small, sd, so, sk = small_scan_batch(zmc, torch, prec, stream)
+    evals = float(sum(sp.evals for sp in small))
+    ops = float(sum(ops_per_eval(sp.integrand_id, sp.N, prec) * sp.evals for sp in small))
+    h = zmc.zmc_batch_create(sd, so, zmc.ZMC_BATCH_GRAPH)
+    info = zmc.zmc_batch_info_get(h)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        zmc.zmc_batch_run(h, stream.cuda_stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        zmc.zmc_batch_run(h, stream.cuda_stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    zmc.zmc_batch_destroy(h)
+    info_d = zmc.zmc_device_info_get()
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    f_max = json.load(open(peaks)).get("sm_max_mhz") if os.path.exists(peaks) else None
+    f_max = f_max or info_d.clock_khz / 1e3
+    peak = info_d.sm_count * 128 * f_max * 1e6 / 1e12
+    tot = sum(step_ms)
+    achieved = ops / (statistics.mean(step_ms) * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": evals * args.steps / (tot * 1e-3), "unit": "evals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec else "f64", "data": "synthetic",
+            "config": {"workload": "batch_small_2048 (2048 small scans, one persistent launch "
+                                   "per precision, CUDA-graph replay)", "scans": len(small),
+                       "tiles": int(info.tiles), "evaluations": evals,
+                       "precision": args.precision,
+                       "l2": "256 MiB buffer written between timed steps"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "batch_kernel (persistent)"},
+            "clocks": clk, "gpu_launches": info.launches_per_run * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch_bench(args, world, rank, local):
     """One step = one run of the 256-scan uneven batch (persistent launch,
     CUDA-graph replay); compared with the same scans as separate launches."""
@@ -454,23 +535,7 @@ def run_batch_bench(args, world, rank, local):
     seq_ms = a.elapsed_time(b)
     # Many small scans (the serving mix's typical request): separate launches
     # are overhead-bound there, one persistent launch is not.
-    small = [s for s in wl.batch_uneven_256(count=2048, seed=7)]
-    for s_ in small:
-        s_.samples = int(min(s_.samples, 1 << 11))
-        s_.lists = [v[:min(len(v), 8)] for v in s_.lists]
-    sd, so, sk = [], [], []
-    for sp in small:
-        vals = torch.tensor(sp.values, dtype=torch.float64, device="cuda")
-        d, k = zmc.make_desc(sp.integrand_id, sp.N, sp.lo, sp.hi, sp.lengths, vals, sp.samples,
-                             sp.trials, sp.seed, prec, mem=zmc.ZMC_MEM_DEVICE)
-        d.stream = stream.cuda_stream
-        m = torch.empty(sp.P, dtype=torch.float64, device="cuda")
-        e = torch.empty_like(m)
-        o = zmc.zmc_scan_out()
-        o.mean, o.err = zmc._ptr(m), zmc._ptr(e)
-        sd.append(d)
-        so.append(o)
-        sk.append((k, vals, m, e))
+    small, sd, so, sk = small_scan_batch(zmc, torch, prec, stream)
     small_evals = float(sum(sp.evals for sp in small))
     hs = zmc.zmc_batch_create(sd, so, zmc.ZMC_BATCH_GRAPH)
     zmc.zmc_batch_run(hs, stream.cuda_stream)
@@ -742,11 +807,13 @@ def main():
     args.warmup = max(args.warmup, 3)
 
     world, rank, local = dist_setup()
-    if args.workload == "batch_uneven_256":
+    if args.workload in ("batch_uneven_256", "batch_small_2048"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":
                               "the reference arm times the oracle on the headline workload"}))
             return 0
+        if args.workload == "batch_small_2048":
+            return run_small_batch_bench(args, world, rank, local)
         return run_batch_bench(args, world, rank, local)
     if args.workload == "precision_stress":
         if args.impl == "reference":
