@@ -573,7 +573,8 @@ int zmc_device_info_get(zmc_device_info* info) {
   cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
   info->clock_khz = clk;
   info->total_mem = ds->prop.totalGlobalMem;
-  std::snprintf(info->name, sizeof(info->name), "%s", ds->prop.name);
+  // the device name, cut to the field's 95 characters
+  std::snprintf(info->name, sizeof(info->name), "%.95s", ds->prop.name);
   return ZMC_OK;
 }
 
