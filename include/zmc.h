@@ -58,6 +58,10 @@ typedef enum {
   ZMC_ENOTFOUND = 7    /* unknown integrand id or ticket         */
 } zmc_status;
 
+/* The FP32 paths form each coordinate y and evaluate g in FP32 (cos/sin/exp on
+ * the special-function unit), so a box far from the origin compared with its
+ * width, or an integrand that cancels strongly, keeps only FP32's 24 bits;
+ * ZMC_FP64 has no such limit.  Per sample the FP32 error is ~1e-7 of g. */
 typedef enum {
   ZMC_FP64 = 0,        /* FP64 samples, integrand and sums                 */
   ZMC_FP32 = 1,        /* FP32 samples and integrand, plain FP32 lane sums  */
