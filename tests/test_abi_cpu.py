@@ -71,6 +71,8 @@ def _desc(lib, **kw):
     ({"first_index": 90, "count": 11}, 1),                    # slice beyond P
     ({"first_index": 100, "count": 0}, 0),                    # empty slice is valid
     ({"gid": 5, "N": 8, "lo": [0] * 8, "hi": [1] * 8, "S": 2 ** 31}, 1),  # S*N too big
+    ({"gid": 5, "N": 8, "lo": [0] * 8, "hi": [1] * 8, "S": 2 ** 31 - 2 ** 17}, 0),  # at the limit
+    ({"gid": 5, "N": 8, "lo": [0] * 8, "hi": [1] * 8, "S": 2 ** 31 - 2 ** 17 + 1}, 1),  # past it
     ({"tiles": (3, 1, 256)}, 1),                              # lanes not a power of 2
     ({"tiles": (32, 1, 100)}, 1),                             # block not multiple of 32
     ({"tiles": (64, 1, 32)}, 1),                              # block below 64
