@@ -180,6 +180,28 @@ def test_every_small_sample_count(zmc, N):
                 assert np.allclose(got["s1"], ref["s1"], rtol=0, atol=(1e-12 if prec == 0 else 1e-5) * S)
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_maximum_samples_per_point(zmc, prec):
+    # The largest S the budget allows at N = 8 (S*N = 2^34 - 2^20): Philox call
+    # indices reach 3.4e9 and the last group holds one sample.  The estimate
+    # agrees with the closed form within its standard error, the pooled error
+    # matches the closed-form one, and the last call's words equal the
+    # oracle's.
+    import closed_forms as cf
+    N, S = 8, 2 ** 31 - 2 ** 17
+    x = 0.3
+    lo, hi = np.zeros(N), np.ones(N)
+    res, out = zmc.scan(5, N, lo, hi, [1], [x], S, 2, 11, precision=prec, want_sums=True)
+    f = cf.integral(cf.G_SINSUM, [x], lo, hi)
+    se = cf.sigma_I(cf.G_SINSUM, [x], lo, hi, S) / np.sqrt(2)
+    assert abs(res["mean"][0] - f) < 5 * se, (res["mean"][0], f, se)
+    assert 0.9 < res["errw"][0] / se < 1.1
+    last_call = (S * N - 1) // 5
+    words = zmc.zmc_stream_words(11, 0, 1, 4 * last_call, 4)
+    O = oracle.default()
+    assert list(words) == [O.word(11, 0, 1, 4 * last_call + i) for i in range(4)]
+
+
 def test_grid_index_beyond_32_bits(zmc):
     big = 70000  # P = 4.9e9 > 2^32: the high counter word of p is non-zero
     spec = wl.ScanSpec("big", wl.G_GAUSS03, 2, -np.ones(2), np.ones(2),
