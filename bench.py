@@ -50,6 +50,50 @@ def ops_per_eval(gid: int, N: int, prec: int) -> int:
     return rng + INTEGRAND_OPS[gid](N) + ACCUM_OPS[prec]
 
 
+# The same algorithmic operations split by the SM pipe that executes them:
+# Philox's 20 wide multiplies per call on the FMA-heavy pipe (4 N per
+# evaluation), its 20 three-input XORs and one logic operation per field on the
+# ALU (5 N), the box map, the integrand's arithmetic and the accumulation on the
+# FP32 (or FP64) pipe, and the integrand's cos/sin/exp on the XU.
+INTEGRAND_FP = {1: lambda N: 2 * N - 1, 2: lambda N: 2 * N + 1, 3: lambda N: 3 * N - 1,
+                4: lambda N: 2 * N + 1, 5: lambda N: N + 1}
+INTEGRAND_XU = {1: lambda N: N, 2: lambda N: 1, 3: lambda N: 0, 4: lambda N: 1,
+                5: lambda N: 1}
+# Lane-operations per clock per SM of each pipe on GB300, measured by the
+# library's instruction-throughput probes (profiles/pipes_gb300.md): the wide
+# multiply interleaved with other work, LOP3, FFMA, MUFU.COS/SIN and MUFU.EX2.
+PIPE_RATE = {"fma_heavy": 32.0, "alu": 64.0, "fp32": 123.7, "xu_cos": 16.0, "xu_ex2": 32.0}
+
+
+def pipe_model(gid: int, N: int, prec: int) -> dict:
+    """SM-cycles per evaluation that each pipe needs for the algorithmic
+    operations of (integrand, N) in an FP32 precision (ops / pipe rate), and
+    the issue slots (all operations / 128 lane-slots per clock per SM)."""
+    if gid == 0:
+        return {}
+    xu_rate = PIPE_RATE["xu_ex2"] if gid == 2 else PIPE_RATE["xu_cos"]
+    cyc = {"fma_heavy": 4.0 * N / PIPE_RATE["fma_heavy"],
+           "alu": 5.0 * N / PIPE_RATE["alu"],
+           "fp32": (N + INTEGRAND_FP[gid](N) + ACCUM_OPS[prec]) / PIPE_RATE["fp32"],
+           "xu": INTEGRAND_XU[gid](N) / xu_rate,
+           "issue": ops_per_eval(gid, N, prec) / 128.0}
+    return cyc
+
+
+def binding_pipe(gid: int, N: int, prec: int, sm_count: int, f_mhz: float,
+                 evals_per_s: float) -> dict:
+    """The pipe whose algorithmic work per evaluation (pipe_model) allows the
+    fewest evaluations per second, that ceiling, and the kernel's share of it."""
+    cyc = pipe_model(gid, N, prec)
+    if not cyc:
+        return {}
+    name = max(cyc, key=cyc.get)
+    ceil = sm_count * f_mhz * 1e6 / cyc[name]
+    return {"pipe": name, "sm_cycles_per_eval": cyc[name], "evals_per_s_at_full_pipe": ceil,
+            "frac": evals_per_s / ceil, "source": "algorithmic operations per pipe "
+            "(bench.py pipe_model) at the probe-measured pipe rates"}
+
+
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
     """nvidia-smi clock/throttle samples every 200 ms while running."""
@@ -446,7 +490,7 @@ def run_small_batch_bench(args, world, rank, local):
                        "tiles": int(info.tiles), "evaluations": evals,
                        "precision": args.precision,
                        "l2": "256 MiB buffer written between timed steps"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "roofline": {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "batch_kernel (persistent)"},
             "clocks": clk, "gpu_launches": info.launches_per_run * args.steps}
@@ -569,7 +613,7 @@ def run_batch_bench(args, world, rank, local):
                        "tiles": int(info.tiles), "evaluations": evals,
                        "precision": args.precision,
                        "l2": "256 MiB buffer written between timed steps"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "roofline": {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "batch_kernel (persistent)"},
             "separate_launches": {"ms": seq_ms, "evals_per_s": evals / (seq_ms * 1e-3),
@@ -606,6 +650,134 @@ def run_serving_bench(args, world, rank, local):
             "serving": res, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def registry_pipe_table() -> dict:
+    """Per-kernel ncu figures of the committed registry profile, keyed
+    (integrand, N, precision); {} when the kernel sources changed since the
+    counters were taken."""
+    from paper_1910_01965_gb300 import build as B
+    from paper_1910_01965_gb300 import ncu_table
+    path = os.path.join(ROOT, "profiles", "registry_pipes_gb300.md")
+    if not os.path.exists(path):
+        return {}
+    stamp, rows = ncu_table.read_summary(path)
+    return rows if stamp == B.source_stamp() else {}
+
+
+def run_registry(args):
+    """Every (integrand, N) of the registry in FP32-Kahan and FP64: one line per
+    kernel with its evaluations/s, its roofline on the SM issue peak from the
+    algorithmic operations, the binding pipe of the algorithmic per-pipe model,
+    and the committed ncu pipe figures of that kernel where they are current.
+    ``--registry-scale small`` runs each kernel once on a small grid (the ncu
+    capture of the registry profile)."""
+    import torch
+    from paper_1910_01965_gb300 import workloads as wl
+    from paper_1910_01965_gb300 import zmc
+    torch.cuda.set_device(0)
+    zmc.load()
+    info = zmc.zmc_device_info_get()
+    f_max, f_src = _f_max(info)
+    small = args.registry_scale == "small"
+    gids = [int(g) for g in args.registry_integrands.split(",")]
+    Ns = [int(n) for n in args.registry_n.split(",")]
+    precs = [p for p in args.registry_precisions.split(",")]
+    table = {} if small else registry_pipe_table()
+    stream = torch.cuda.current_stream()
+    flush = None if small else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    peak_issue = info.sm_count * 128 * f_max * 1e6 / 1e12
+    summary = []
+    for gid in gids:
+        for N in Ns:
+            if small:
+                spec = wl.registry_scan(gid, N, points=10_000, samples=1 << 13)
+            else:
+                spec = wl.registry_scan(gid, N)
+            vals = torch.tensor(spec.values, dtype=torch.float64, device="cuda")
+            mean = torch.empty(spec.P, dtype=torch.float64, device="cuda")
+            err = torch.empty_like(mean)
+            for pname in precs:
+                p = zmc.PRECISIONS[pname]
+
+                def run(count=-1):
+                    return zmc.scan_device(spec.integrand_id, spec.N, spec.lo, spec.hi,
+                                           spec.lengths, vals, spec.samples, spec.trials,
+                                           spec.seed, mean, err, precision=p,
+                                           stream=stream.cuda_stream,
+                                           flags=zmc.ZMC_F_TIMINGS, count=count)
+                if small:
+                    run()
+                    continue
+                run(count=min(spec.P, 64))            # load the kernel, warm the clocks
+                steps = args.registry_steps if p != zmc.ZMC_FP64 else 1
+                kms, tms = [], []
+                for _ in range(steps):
+                    flush.zero_()
+                    o = run()
+                    kms.append(o.kernel_ms)
+                    tms.append(o.kernel_ms + o.finalize_ms)
+                k_ms = statistics.mean(kms)
+                rate = spec.evals / (k_ms * 1e-3)
+                line = {"metric": METRIC, "workload": "registry", "integrand": gid,
+                        "N": N, "precision": pname, "value": spec.evals / (
+                            statistics.mean(tms) * 1e-3), "unit": "evals/s",
+                        "kernel_evals_per_s": rate, "kernel_ms": k_ms, "steps": steps,
+                        "config": dict(spec.describe(), tiles=[o.tile_lanes, o.tile_splits,
+                                                               o.tile_block])}
+                if p != zmc.ZMC_FP64:
+                    ops = ops_per_eval(gid, N, p)
+                    achieved = ops * rate / 1e12
+                    line["roofline"] = {"bound": "issue", "achieved": achieved,
+                                        "peak": peak_issue, "unit": "Tops/s",
+                                        "frac": achieved / peak_issue, "ops_per_eval": ops,
+                                        "traffic": None,
+                                        "peak_basis": "%d SMs x 128 lane-slots x %.0f MHz (%s)"
+                                                      % (info.sm_count, f_max, f_src)}
+                    line["binding_pipe"] = binding_pipe(gid, N, p, info.sm_count, f_max, rate)
+                m = table.get((gid, N, p))
+                if m:
+                    meas = {"source": "profiles/registry_pipes_gb300.md (ncu, small grid)"}
+                    for pipe in ("heavy", "alu", "lite", "xu", "fp64"):
+                        per_sm = pipe == "fp64"     # one FP64 unit per SM, else per SMSP
+                        cyc = m.get(pipe + ("_sm_cycles_per_eval" if per_sm
+                                            else "_smsp_cycles_per_eval"))
+                        if cyc:
+                            ceil = info.sm_count * (1 if per_sm else 4) * f_max * 1e6 / cyc
+                            meas[pipe] = {"smsp_cycles_per_eval": cyc,
+                                          "evals_per_s_at_full_pipe": ceil,
+                                          "frac": rate / ceil}
+                    meas["registers"] = m.get("registers")
+                    meas["inst_per_eval"] = m.get("inst_per_eval")
+                    line["measured_pipes"] = meas
+                    if p == zmc.ZMC_FP64 and m.get("fp64_sm_cycles_per_eval"):
+                        line["roofline"] = {
+                            "bound": "fp64", "frac": meas["fp64"]["frac"],
+                            "basis": "FP64-pipe cycles per evaluation measured by ncu (the "
+                                     "FP64 cos/exp/sin are library routines; their operation "
+                                     "counts are not part of the method)"}
+                print(json.dumps(line), flush=True)
+                summary.append(line)
+            del vals, mean, err
+    if small:
+        print(json.dumps({"workload": "registry", "scale": "small", "kernels": len(gids) *
+                          len(Ns) * len(precs)}), flush=True)
+        return 0
+    fp32 = [l_ for l_ in summary if "binding_pipe" in l_ and l_["binding_pipe"]]
+    worst = min(fp32, key=lambda l_: l_["binding_pipe"]["frac"]) if fp32 else None
+    print(json.dumps({"workload": "registry", "summary": True, "kernels": len(summary),
+                      "worst_fp32_binding_frac": worst and worst["binding_pipe"]["frac"],
+                      "worst_fp32_kernel": worst and [worst["integrand"], worst["N"]]}),
+          flush=True)
+    return 0
+
+
+def _f_max(info):
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    f_max = json.load(open(peaks)).get("sm_max_mhz") if os.path.exists(peaks) else None
+    if f_max:
+        return f_max, "sm_max_mhz of MEASURED_PEAKS.json"
+    return info.clock_khz / 1e3, "device-reported maximum SM clock"
 
 
 # Printed in the paper (Table 1, Sec. 3.1; one V100 + Xeon Silver 4110, times in
@@ -803,6 +975,13 @@ def main():
     ap.add_argument("--tune-ms", type=int, default=300)
     ap.add_argument("--table-samples", type=int, default=10_000)
     ap.add_argument("--stress-points", type=int, default=48)
+    ap.add_argument("--registry-scale", default="full", choices=["full", "small"])
+    ap.add_argument("--registry-integrands", default="1,2,3,4,5")
+    ap.add_argument("--registry-n", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--registry-precisions", default="fp32_kahan,fp64")
+    ap.add_argument("--registry-steps", type=int, default=3)
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs: the whole grid per rank (own seed), weak scaling")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -815,6 +994,12 @@ def main():
         if args.workload == "batch_small_2048":
             return run_small_batch_bench(args, world, rank, local)
         return run_batch_bench(args, world, rank, local)
+    if args.workload == "registry":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the reference arm times the oracle on the headline workload"}))
+            return 0
+        return run_registry(args)
     if args.workload == "precision_stress":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":
@@ -846,20 +1031,34 @@ def main():
         return run_reference(args, spec, world, rank)
 
     import torch
+    from paper_1910_01965_gb300 import shard
     from paper_1910_01965_gb300 import zmc
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-        spec.seed = spec.seed + rank  # an independent problem per rank
+        if args.replicas:
+            spec.seed = spec.seed + rank  # an independent problem per rank
     zmc.load()
     info = zmc.zmc_device_info_get()
     prec = zmc.PRECISIONS[args.precision]
+    # Several GPUs: each rank scans its contiguous slice of the one grid
+    # (strong scaling, no exchange but the host gather), with the tiles the
+    # planner picks for the whole grid, so the gathered result equals a
+    # one-GPU scan bit for bit; --replicas gives each rank the whole grid
+    # under its own seed instead (weak scaling).
+    partition = world > 1 and not args.replicas
+    first, count = shard.shard_range(spec.P, rank, world) if partition else (0, spec.P)
+    plan = zmc.scan(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
+                    spec.samples, spec.trials, spec.seed, precision=prec,
+                    flags=zmc.ZMC_F_PLAN_ONLY)[1]
+    tiles = (plan.tile_lanes, plan.tile_splits, plan.tile_block) if partition else (0, 0, 0)
+    rank_evals = count * spec.trials * spec.samples
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     vals = torch.tensor(spec.values, dtype=torch.float64, device=dev)
-    mean = torch.empty(spec.P, dtype=torch.float64, device=dev)
+    mean = torch.empty(count, dtype=torch.float64, device=dev)
     err = torch.empty_like(mean)
     errw = torch.empty_like(mean)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -867,7 +1066,8 @@ def main():
     def step(p=prec, flags=zmc.ZMC_F_TIMINGS):
         return zmc.scan_device(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
                                vals, spec.samples, spec.trials, spec.seed, mean, err, errw,
-                               precision=p, stream=stream.cuda_stream, flags=flags)
+                               precision=p, stream=stream.cuda_stream, flags=flags,
+                               first_index=first, count=count, tiles=tiles)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -894,11 +1094,11 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(world, sum(step_ms))
-    value = world * spec.evals * args.steps / (total_ms * 1e-3)
+    job_evals = spec.evals if partition else world * spec.evals
+    value = job_evals * args.steps / (total_ms * 1e-3)
 
-    # roofline of the sampling kernel (the dominant one)
-    n_us = spec.P * spec.trials * o.tile_splits
-    ops = ops_per_eval(spec.integrand_id, spec.N, prec) * spec.evals
+    # roofline of the sampling kernel (the dominant one), this rank's launches
+    ops = ops_per_eval(spec.integrand_id, spec.N, prec) * rank_evals
     k_ms = statistics.mean(kernel_ms)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     f_max = None
@@ -910,47 +1110,68 @@ def main():
     peak = info.sm_count * 128 * f_max * 1e6 / 1e12   # lane-ops per second, T
     achieved = ops / (k_ms * 1e-3) / 1e12
     figs = profile_figures(spec) if prec == zmc.ZMC_FP32_KAHAN else {}
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+    prof_src = "profiles/scan_kernel_gauss03_N4_fp32k.md (ncu; read by bench.py, " \
+               "valid while the kernel sources are unchanged)"
+    roofline = {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": figs.get("traffic_bytes_per_launch"),
+                "traffic_source": prof_src if "traffic_bytes_per_launch" in figs else None,
                 "kernel": "scan_kernel (sampling)", "kernel_ms": k_ms,
                 "ops_per_eval": ops_per_eval(spec.integrand_id, spec.N, prec),
-                "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s)" % (
+                "peak_basis": "%d SMs x 128 lane-slots x %.0f MHz (%s)" % (
                     info.sm_count, f_max, f_src)}
+    kernel_rate = rank_evals / (k_ms * 1e-3)
+    if prec != zmc.ZMC_FP64:
+        roofline["binding_pipe_model"] = binding_pipe(spec.integrand_id, spec.N, prec,
+                                                      info.sm_count, f_max, kernel_rate)
     if "heavy_smsp_cycles_per_eval" in figs:
         # the pipe that binds: each SMSP's FMA-heavy pipe, cycles per evaluation
         # from the committed ncu counters; its ceiling at the same clock
         cyc = figs["heavy_smsp_cycles_per_eval"]
         ceil = info.sm_count * 4 * f_max * 1e6 / cyc
-        kernel_rate = spec.evals / (k_ms * 1e-3)
         roofline["binding_pipe"] = {"pipe": "FMA-heavy", "smsp_cycles_per_eval": cyc,
                                     "evals_per_s_at_full_pipe": ceil,
-                                    "frac": kernel_rate / ceil}
+                                    "frac": kernel_rate / ceil, "source": prof_src}
 
-    # end to end through the C ABI with host buffers (pinned)
+    # end to end through the C ABI with host buffers (pinned); with several
+    # GPUs each rank's slice, the slowest rank's time (shard.sharded_scan)
     h_vals = torch.tensor(spec.values, dtype=torch.float64).pin_memory().numpy()
-    h_mean = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
-    h_err = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+    h_mean = torch.empty(count, dtype=torch.float64).pin_memory().numpy()
+    h_err = torch.empty(count, dtype=torch.float64).pin_memory().numpy()
     d_host, keep = zmc.make_desc(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
-                                 h_vals, spec.samples, spec.trials, spec.seed, prec)
+                                 h_vals, spec.samples, spec.trials, spec.seed, prec,
+                                 first_index=first, count=count, tiles=tiles)
     o_host = zmc.zmc_scan_out()
     o_host.mean = h_mean.ctypes.data_as(zmc._dp)
     o_host.err = h_err.ctypes.data_as(zmc._dp)
     zmc.zmc_scan_ex(d_host, o_host)        # warm
     e2e_steps = max(3, min(args.steps, 5))
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        zmc.zmc_scan_ex(d_host, o_host)
-    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
-    e2e = {"value": world * spec.evals * e2e_steps / e2e_s, "unit": "evals/s",
-           "h2d_bytes_per_step": int(h_vals.nbytes),
-           "d2h_bytes_per_step": int(h_mean.nbytes + h_err.nbytes),
+
+    def e2e_pass(f0, c0):
+        for _ in range(e2e_steps):
+            zmc.zmc_scan_ex(d_host, o_host)
+        return {"mean": h_mean}
+    if partition:
+        gathered, e2e_s = shard.sharded_scan(spec.P, e2e_pass)
+    else:
+        barrier(world)
+        t0 = time.perf_counter()
+        e2e_pass(0, spec.P)
+        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": job_evals * e2e_steps / e2e_s, "unit": "evals/s",
+           "h2d_bytes_per_step": int(h_vals.nbytes) * world,
+           "d2h_bytes_per_step": int(h_mean.nbytes + h_err.nbytes) * world,
            "steps": e2e_steps, "api": "zmc_scan_ex (ZMC_MEM_HOST, pinned host buffers)"}
 
     extra = {}
     got = {"mean": mean.cpu().numpy(), "err": err.cpu().numpy()}
+    if partition:                          # the whole grid from every rank's slice
+        got = {k: shard.gather_slices(v, spec.P) for k, v in got.items()}
+        extra["partition"] = {"ranks": world, "slice_points": count,
+                              "tiles": list(tiles),
+                              "e2e_gather_equals_device": bool(np.array_equal(
+                                  gathered["mean"], got["mean"]))}
     got64 = None
-    if rank == 0 and not args.no_fp64 and prec != zmc.ZMC_FP64:
+    if rank == 0 and not args.no_fp64 and prec != zmc.ZMC_FP64 and not partition:
         step(zmc.ZMC_FP64, zmc.ZMC_F_SYNC)  # warm the FP64 kernel
         o64 = step(zmc.ZMC_FP64)
         got64 = {"mean": mean.cpu().numpy(), "err": err.cpu().numpy()}
@@ -974,11 +1195,13 @@ def main():
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if partition else "weak", "vs_baseline": None,
             "dtype": "f64" if prec == zmc.ZMC_FP64 else "f32",
             "data": "synthetic",
             "config": dict(spec.describe(), precision=args.precision,
-                           parallelism="independent scan per GPU" if world > 1 else "1 GPU",
+                           parallelism=("contiguous slice of the grid per GPU" if partition
+                                        else "independent scan per GPU" if world > 1
+                                        else "1 GPU"),
                            tiles=[o.tile_lanes, o.tile_splits, o.tile_block],
                            l2="256 MiB buffer written between timed steps"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define ZMC_ABI_VERSION 1
+#define ZMC_ABI_VERSION 2
 #define ZMC_MAX_N 8   /* integration dimensions   */
 #define ZMC_MAX_M 16  /* parameters (value lists) */
 
@@ -122,6 +122,20 @@ enum {
  *                       sample splits per (point, trial) unit, and threads
  *                       per block (64..512, multiple of 32)
  *  flags                ZMC_F_* bits
+ *  chunk_points         zmc_scan_ex cuts the slice into chunks of this many
+ *                       consecutive grid points (the batches of Sec. 2);
+ *                       0 = chosen by the library: as many points as keep
+ *                       one chunk's FP64 partial sums within 256 MiB and,
+ *                       with host buffers, at most 1/8 of the slice (never
+ *                       fewer than 2^20 points).  Every chunk uses the tile
+ *                       plan of the whole call, so the results do not depend
+ *                       on the chunking (bit for bit).  With host buffers and
+ *                       more than one chunk, the device->host copy of chunk k
+ *                       runs on a copy stream while chunk k+1 computes
+ *                       (straight into the caller's arrays when they are
+ *                       pinned, else through pinned staging buffers that the
+ *                       library keeps for reuse).  >= 0; the server and the
+ *                       batch calls ignore it.
  */
 typedef struct zmc_scan_desc {
   int integrand_id;
@@ -145,6 +159,7 @@ typedef struct zmc_scan_desc {
   int tile_splits;
   int tile_block;
   int flags;
+  int64_t chunk_points;
 } zmc_scan_desc;
 
 /*
@@ -153,7 +168,8 @@ typedef struct zmc_scan_desc {
  * per-trial sums sum_s g and sum_s g^2, count*T entries, trial fastest.
  * All arrays are host or device memory according to desc->mem.
  * The remaining fields are written by the call: the tile configuration it
- * used and, with ZMC_F_TIMINGS, CUDA-event times in milliseconds.
+ * used, the number of chunks and, with ZMC_F_TIMINGS, CUDA-event times in
+ * milliseconds (kernel_ms and finalize_ms summed over the chunks).
  */
 typedef struct zmc_scan_out {
   double* mean;
@@ -168,8 +184,10 @@ typedef struct zmc_scan_out {
   float h2d_ms;        /* host->device copies (ZMC_MEM_HOST only)          */
   float kernel_ms;     /* the sampling kernel                              */
   float finalize_ms;   /* the cross-split reduction and statistics kernel  */
-  float d2h_ms;        /* device->host copies (ZMC_MEM_HOST only)          */
+  float d2h_ms;        /* device->host copies (ZMC_MEM_HOST only) not
+                          hidden behind the sampling of later chunks       */
   float total_ms;      /* first event to last event                        */
+  int64_t chunks;      /* chunks the slice was cut into (see chunk_points) */
 } zmc_scan_out;
 
 typedef struct zmc_integrand_info {
@@ -216,8 +234,9 @@ int zmc_validate(const zmc_scan_desc* d);
 
 /*
  * Device scratch that zmc_scan_ex needs for `d` with its tile configuration
- * (after planning): 16 bytes per (point, trial, split) for the FP64 partial
- * sums, plus the device copy of the lists and of the outputs when
+ * (after planning): 16 bytes per (point, trial, split) of one chunk for the
+ * FP64 partial sums, plus the device copy of the lists and of the outputs of
+ * one chunk (two when the slice takes several chunks) when
  * d->mem == ZMC_MEM_HOST.  Touches no GPU when the tiles are given
  * explicitly; otherwise it may query the device for its SM count.
  */
@@ -248,6 +267,22 @@ int zmc_stream_words(uint64_t seed, int64_t p, int t, uint64_t first_word,
                      int64_t nwords, uint32_t* out);
 
 /*
+ * Device-side checks.  A library built with -DZMC_DEBUG=1 (libzmc_debug.so,
+ * paper_1910_01965_gb300/build.py --debug) checks every grid index, list
+ * digit and offset, staged-table slot, batch tile and partial-sum slot before
+ * the access; a failed check skips the access and is recorded on the device
+ * (nothing traps).  zmc_scan_ex then waits for its work and fails with
+ * ZMC_ECUDA and a message if a check failed.  This call waits for the current
+ * device, returns the number of failed checks recorded since the last call
+ * (the first one's check code and index in *code and *index, either may be
+ * NULL) and clears them; it returns -1 in a build without checks.  Check
+ * codes: 1 grid index outside the slice, 2 list digit or offset out of range,
+ * 3 staged-list slot beyond the shared memory, 4 partial-sum slot, 5 batch
+ * tile, 6 finalize index.  The paper has no counterpart (a test aid).
+ */
+int64_t zmc_debug_failures(unsigned* code, long long* index);
+
+/*
  * A scan that allocates nothing.  The paper has no counterpart: this serves
  * callers that cannot call cudaMalloc (or any allocator) when they scan —
  * code on a latency-critical path, where an allocation can wait on the
@@ -255,20 +290,29 @@ int zmc_stream_words(uint64_t seed, int64_t p, int t, uint64_t first_word,
  * all device memory through its own allocator and budget; hosts that fix
  * their device footprint at start-up.
  *
- * Same computation, kernels and results as zmc_scan_ex.  d->mem must be
- * ZMC_MEM_DEVICE (lists and outputs in caller-owned device memory),
- * d->workspace NULL, and ZMC_F_TIMINGS unset; ZMC_F_SYNC is honoured.  Work
- * is enqueued on d->stream (NULL = the CUDA default stream).
+ * Same computation and kernels as zmc_scan_ex, and the same tile plan (the
+ * autotuner's entry for the scan's class when the tiles are left open, else
+ * the fixed rules), so the results equal zmc_scan_ex's bit for bit.
+ * d->mem must be ZMC_MEM_DEVICE (lists and outputs in caller-owned device
+ * memory), d->workspace NULL, and ZMC_F_TIMINGS unset; ZMC_F_SYNC is
+ * honoured, and ZMC_F_PLAN_ONLY fills the tile fields and returns without
+ * computing.  The slice is not chunked (chunk_points is ignored).  Work is
+ * enqueued on d->stream (NULL = the CUDA default stream).
  *
  * Scratch: the FP64 partial sums live in a file-scope device array of
- * ZMC_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the library
- * holds until the process exits.  A call whose partial sums
+ * ZMC_NOALLOC_SCRATCH_BYTES (16 MiB).  A call whose partial sums
  * (points x trials x sample splits x 16 bytes) exceed it returns ZMC_EINVAL
- * with a message; scan a smaller slice (first_index, count) per call.  The
- * first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents;
- * nothing in it needs clearing, but calls that overlap on the GPU race on it.
+ * with a message; scan a smaller slice (first_index, count) per call.
+ * CUDA loads device code lazily: the first call on a device loads the module
+ * that holds the array, which reserves its 16 MiB there, looks up its device
+ * address (once per device, with that device current) and reads the
+ * autotuner's cache file if ZMC_AUTOTUNE_CACHE names one.  That first call can
+ * therefore allocate, wait on the driver, or fail with ZMC_ENOMEM/ZMC_ECUDA;
+ * make it once at start-up (a small warm-up scan), before any stream capture.
+ * Later calls on that device allocate nothing; the device holds the array
+ * until the process exits.  All calls share the array and it keeps the last
+ * call's contents; nothing in it needs clearing, but calls that overlap on
+ * the GPU race on it.
  */
 #define ZMC_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 int zmc_scan_noalloc(const zmc_scan_desc* d, zmc_scan_out* o);

@@ -21,6 +21,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libzmc.so")
+# The checking build: the same sources with ZMC_DEBUG=1 (device-side bounds
+# checks that record failures instead of accessing out of range).
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libzmc_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -125,5 +129,14 @@ def build(force: bool = False, jobs: int = 0, verbose: bool = False,
     return lib
 
 
+def build_debug(force: bool = False) -> str:
+    """libzmc_debug.so: every kernel with its ZMC_DEBUG bounds checks."""
+    return build(force=force, extra_flags=("-DZMC_DEBUG=1",), lib=LIB_DEBUG,
+                 build_dir=BUILD_DEBUG)
+
+
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    if "--debug" in sys.argv:
+        print(build_debug(force="--force" in sys.argv))
+    else:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

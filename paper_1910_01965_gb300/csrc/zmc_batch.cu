@@ -11,6 +11,7 @@
 #include "../../include/zmc_batch.h"
 #include "zmc_internal.h"
 #include "zmc_runtime.h"
+#include "zmc_trace.h"
 
 namespace zmc {
 
@@ -119,6 +120,8 @@ static int enqueue_run(zmc_batch* b, cudaStream_t s, cudaEvent_t mid) {
     ba.tiles = b->d_tiles + g.tile_begin;
     ba.ntiles = g.tile_end - g.tile_begin;
     ba.counter = g.counter;
+    ba.nscans = b->n;
+    ba.dbg = debug_words();
     const int le = batch_launch(g.precision, ba, g.grid, kBatchBlock, g.smem, s);
     if (le != 0) return cuda_fail(static_cast<cudaError_t>(le), "batched kernel launch");
   }
@@ -236,6 +239,7 @@ int batch_create(const zmc_scan_desc* d, zmc_scan_out* o, int n, int flags, zmc_
     f.errw = o[i].errw;
     f.s1 = o[i].s1;
     f.s2 = o[i].s2;
+    f.dbg = b->args[i].dbg;
   }
 
   // Tiles: grouped by precision; within a group the scans with the longest
@@ -350,11 +354,18 @@ extern "C" {
 int zmc_batch_create(const zmc_scan_desc* d, zmc_scan_out* o, int n, int flags,
                      zmc_batch** out) {
   clear_error();
-  return batch_create(d, o, n, flags, out);
+  TraceRange trace("zmc_batch_create");
+  const int rc = batch_create(d, o, n, flags, out);
+  if (rc == ZMC_OK)
+    log_msg(2, "batch: %d scans, %lld tiles, %lld evaluations, %d launches per run%s", n,
+            (long long)(*out)->ntiles, (long long)(*out)->evals, (*out)->launches,
+            (*out)->exec ? ", CUDA graph" : "");
+  return rc;
 }
 
 int zmc_batch_run(zmc_batch* b, void* stream) {
   clear_error();
+  TraceRange trace("zmc_batch_run");
   return batch_run(b, static_cast<cudaStream_t>(stream), nullptr);
 }
 

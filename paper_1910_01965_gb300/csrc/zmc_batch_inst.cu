@@ -60,7 +60,7 @@ __device__ __noinline__ void batch_tile(const ScanArgs& a, const BatchTile& t, b
   if (active) unit_split_lane<N, F, PREC>(a, rk0, rk1, table, dimc, us, lane, acc);
   double s1 = acc.sum1(), s2 = acc.sum2();
   reduce_unit_split(a, s1, s2, red);
-  if (lane == 0 && active) {
+  if (lane == 0 && active && ZMC_CHECK(a.dbg, us >= 0 && us < a.n_us, kDbgPartialSlot, us)) {
     a.partial[2 * us] = s1;
     a.partial[2 * us + 1] = s2;
   }
@@ -89,18 +89,20 @@ batch_kernel(const __grid_constant__ BatchArgs b) {
     const long long tile = s_tile;
     if (tile >= b.ntiles) break;
     const BatchTile t = b.tiles[tile];
-    const ScanArgs& a = b.scans[t.scan];
-    const bool restage = t.scan != staged;
-    staged = t.scan;
-    switch (a.gid * 8 + a.N - 1) {
-      ZMC_CASES(ZMC_G_CONST, ZMC_BF(Const))
-      ZMC_CASES(ZMC_G_COSPROD, ZMC_BF(CosProd))
-      ZMC_CASES(ZMC_G_GAUSS03, ZMC_BF(Gauss))
-      ZMC_CASES(ZMC_G_POLY, ZMC_BF(Poly))
-      ZMC_CASES(ZMC_G_OSC01, ZMC_BF(Osc))
-      ZMC_CASES(ZMC_G_SINSUM, ZMC_BF(SinSum))
-      default:
-        break;
+    if (ZMC_CHECK(b.dbg, t.scan >= 0 && t.scan < b.nscans && t.units >= 0, kDbgTile, tile)) {
+      const ScanArgs& a = b.scans[t.scan];
+      const bool restage = t.scan != staged;
+      staged = t.scan;
+      switch (a.gid * 8 + a.N - 1) {
+        ZMC_CASES(ZMC_G_CONST, ZMC_BF(Const))
+        ZMC_CASES(ZMC_G_COSPROD, ZMC_BF(CosProd))
+        ZMC_CASES(ZMC_G_GAUSS03, ZMC_BF(Gauss))
+        ZMC_CASES(ZMC_G_POLY, ZMC_BF(Poly))
+        ZMC_CASES(ZMC_G_OSC01, ZMC_BF(Osc))
+        ZMC_CASES(ZMC_G_SINSUM, ZMC_BF(SinSum))
+        default:
+          break;
+      }
     }
     __syncthreads();  // the tile is done before shared memory or s_tile is reused
   }

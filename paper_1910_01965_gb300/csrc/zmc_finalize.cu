@@ -65,7 +65,9 @@ __global__ void finalize_batch_kernel(const __grid_constant__ FinalizeBatchArgs 
     const int mid = (lo + hi + 1) >> 1;
     if (b.prefix[mid] <= i) lo = mid; else hi = mid - 1;
   }
-  finalize_point(b.fa[lo], i - b.prefix[lo]);
+  const int64_t k = i - b.prefix[lo];
+  if (ZMC_CHECK(b.fa[lo].dbg, k >= 0 && k < b.fa[lo].count, kDbgFinalize, i))
+    finalize_point(b.fa[lo], k);
 }
 
 int finalize_batch_launch(const FinalizeBatchArgs& a, void* stream) {

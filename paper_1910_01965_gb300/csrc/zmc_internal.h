@@ -16,6 +16,24 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 // Largest list staging in shared memory (doubles).
 constexpr int kMaxSmemVals = 4096;
 
+// ---------------------------------------------------------- debug checks --
+// Builds with -DZMC_DEBUG=1 check every grid index, list digit and offset,
+// staged-table slot, batch tile and partial-sum slot before the access.  A
+// failed check skips the access (a safe index is used instead) and records
+// itself in three device words [code of the first failure, its index, number
+// of failures]; nothing traps.  Release builds compile the checks away.
+#ifndef ZMC_DEBUG
+#define ZMC_DEBUG 0
+#endif
+enum {
+  kDbgGridIndex = 1,    // a unit's grid index outside the slice
+  kDbgListOffset = 2,   // a mixed-radix digit or list offset out of range
+  kDbgStagedTable = 3,  // a staged-list slot beyond the dynamic shared memory
+  kDbgPartialSlot = 4,  // a partial-sum slot beyond the launch's unit-splits
+  kDbgTile = 5,         // a batch tile or its scan out of range
+  kDbgFinalize = 6      // a finalize index beyond its scan's points
+};
+
 // Everything one launch of the sampling kernel needs, passed by value.
 // A "unit" is one (grid point, trial) pair; its S samples are cut into
 // `splits` contiguous ranges of sample groups, and each range (a
@@ -45,6 +63,7 @@ struct ScanArgs {
   uint32_t rk0[10];     // Philox round keys: key0 + r * W0
   uint32_t rk1[10];     // Philox round keys: key1 + r * W1
   double* partial;      // device, [n_us][2] FP64 (sum g, sum g^2)
+  unsigned long long* dbg;  // device check words (ZMC_DEBUG builds), or null
 };
 
 struct FinalizeArgs {
@@ -59,6 +78,7 @@ struct FinalizeArgs {
   double* errw;   // may be null
   double* s1;     // may be null, [count][T]
   double* s2;     // may be null, [count][T]
+  unsigned long long* dbg = nullptr;  // device check words (ZMC_DEBUG builds)
 };
 
 // Each Philox call gives five 23-bit fields.  Samples per group G and calls
@@ -89,6 +109,8 @@ struct BatchArgs {
   const BatchTile* tiles;         // [ntiles], device, in the order they are taken
   int64_t ntiles;
   unsigned long long* counter;    // device; zeroed before each launch
+  int32_t nscans = 0;             // entries of scans (checked in ZMC_DEBUG builds)
+  unsigned long long* dbg = nullptr;  // device check words (ZMC_DEBUG builds)
 };
 
 struct FinalizeBatchArgs {
@@ -107,5 +129,29 @@ int finalize_batch_launch(const FinalizeBatchArgs& a, void* stream);
 
 int stream_words_launch(uint64_t seed, int64_t p, int t, uint64_t first_word,
                         int64_t nwords, uint32_t* out_dev, void* stream);
+
+#ifdef __CUDACC__
+#if ZMC_DEBUG
+// Record a failed check (first failure's code and index, failure count).
+__device__ __forceinline__ bool dbg_ok(unsigned long long* w, bool ok, unsigned code,
+                                       long long index) {
+  if (!ok && w) {
+    if (atomicCAS(&w[0], 0ull, static_cast<unsigned long long>(code)) == 0ull)
+      w[1] = static_cast<unsigned long long>(index);
+    atomicAdd(&w[2], 1ull);
+  }
+  return ok;
+}
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+  unsigned v;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
+#define ZMC_CHECK(w, cond, code, index) \
+  ::zmc::dbg_ok((w), (cond), (code), static_cast<long long>(index))
+#else
+#define ZMC_CHECK(w, cond, code, index) true
+#endif
+#endif  // __CUDACC__
 
 }  // namespace zmc

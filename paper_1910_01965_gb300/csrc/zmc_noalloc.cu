@@ -11,11 +11,17 @@
 // fixed size instead of an allocation.  The caller still passes the lists and
 // the outputs in device memory.
 //
-// The array is kNoAllocScratchBytes (16 MiB, 2^20 partial-sum pairs).  Every
-// GPU that loads the library holds it until the process exits.  All calls
-// share it and it keeps the last call's contents; nothing in it needs to
-// start at zero (the sampling kernel writes every slot the finalize kernel
-// reads), but calls that overlap on the GPU race on it.
+// The array is kNoAllocScratchBytes (16 MiB, 2^20 partial-sum pairs).  CUDA
+// loads a library's device code lazily, so the array is reserved on a device
+// when the first call there loads this module: that first call (which also
+// looks up the array's address and reads the autotuner's cache file, if one is
+// named) may allocate, wait on the driver or fail with ZMC_ENOMEM, and callers
+// with a fixed footprint should make it once at start-up, before any stream
+// capture.  Later calls allocate nothing, and the device keeps the array until
+// the process exits.  All calls share it and it keeps the last call's
+// contents; nothing in it needs to start at zero (the sampling kernel writes
+// every slot the finalize kernel reads), but calls that overlap on the GPU
+// race on it.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -23,6 +29,7 @@
 
 #include "zmc_internal.h"
 #include "zmc_runtime.h"
+#include "zmc_trace.h"
 
 namespace zmc {
 
@@ -33,13 +40,25 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles
 
 // Device address of the array, looked up once per device with that device
 // current.  In host code `g_noalloc_scratch` names a host-side stand-in, not
-// device memory, so only this address may be handed to a kernel.
+// device memory, so only this address may be handed to a kernel.  Each call
+// checks that the recorded address is still device memory of the current
+// device (a pointer-attribute query, no allocation) and looks it up again if
+// not, e.g. after cudaDeviceReset gave the device a new context.
 struct NoAllocSlot {
   bool ready = false;
   double* ptr = nullptr;
 };
 static std::mutex g_noalloc_mu;
 static NoAllocSlot g_noalloc_slot[64];
+
+static bool still_mapped(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
 
 static int noalloc_scratch(double** out) {
   int dev = 0;
@@ -48,6 +67,7 @@ static int noalloc_scratch(double** out) {
   if (dev < 0 || dev >= 64) return fail(ZMC_ECUDA, "device index %d out of range", dev);
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   NoAllocSlot& s = g_noalloc_slot[dev];
+  if (s.ready && !still_mapped(s.ptr, dev)) s.ready = false;
   if (!s.ready) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -69,6 +89,7 @@ static bool device_accessible(const void* p) {
 }
 
 static int scan_noalloc(const zmc_scan_desc* d, zmc_scan_out* o) {
+  TraceRange trace("zmc_scan_noalloc");
   int64_t P = 0, count = 0;
   int rc = validate(d, &P, &count);
   if (rc != ZMC_OK) return rc;
@@ -81,20 +102,24 @@ static int scan_noalloc(const zmc_scan_desc* d, zmc_scan_out* o) {
     return fail(ZMC_EINVAL, "zmc_scan_noalloc takes no workspace (its scratch is built in)");
   if (d->flags & ZMC_F_TIMINGS)
     return fail(ZMC_EINVAL, "zmc_scan_noalloc does not record timings");
-  if (count > 0 && (!o->mean || !o->err)) return fail(ZMC_EINVAL, "mean/err output is NULL");
+  const bool plan_only = (d->flags & ZMC_F_PLAN_ONLY) != 0;
+  if (count > 0 && !plan_only && (!o->mean || !o->err))
+    return fail(ZMC_EINVAL, "mean/err output is NULL");
   const void* ptrs[6] = {d->list_vals, o->mean, o->err, o->errw, o->s1, o->s2};
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 6 && !plan_only; ++i)
     if (ptrs[i] && !device_accessible(ptrs[i]))
       return fail(ZMC_EINVAL, "zmc_scan_noalloc given a pointer that is not device memory");
 
-  // Tile plan from the device's SM count (an attribute query, no allocation).
+  // The tile plan zmc_scan_ex would make (the autotuner's entry for the
+  // scan's class, else the fixed rules) from the device's SM count: an
+  // attribute query and memory reads, no allocation.
   int dev = 0, sm = 0, tps = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&tps, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-  const TilePlan tp = plan_tiles(d->N, d->samples_per_point, d->trials, count, sm, tps,
-                                 d->tile_lanes, d->tile_splits, d->tile_block);
+  if (!d->tile_lanes && !d->tile_splits && !d->tile_block) tune_ensure_loaded();
+  const TilePlan tp = plan_with(d, count, sm, tps);
   const double need = static_cast<double>(count) * d->trials * tp.splits * 2 * sizeof(double);
   if (need > static_cast<double>(kNoAllocScratchBytes))
     return fail(ZMC_EINVAL,
@@ -106,8 +131,9 @@ static int scan_noalloc(const zmc_scan_desc* d, zmc_scan_out* o) {
   o->tile_splits = tp.splits;
   o->tile_block = tp.block;
   o->launches = 0;
+  o->chunks = count > 0 ? 1 : 0;
   o->h2d_ms = o->kernel_ms = o->finalize_ms = o->d2h_ms = o->total_ms = 0.0f;
-  if (count == 0) return ZMC_OK;
+  if (count == 0 || plan_only) return ZMC_OK;
 
   double* scratch = nullptr;
   rc = noalloc_scratch(&scratch);
@@ -131,6 +157,7 @@ static int scan_noalloc(const zmc_scan_desc* d, zmc_scan_out* o) {
   f.errw = o->errw;
   f.s1 = o->s1;
   f.s2 = o->s2;
+  f.dbg = a.dbg;
   const int fe = finalize_launch(f, stream);
   if (fe != 0) return cuda_fail(static_cast<cudaError_t>(fe), "finalize kernel launch");
   o->launches = 2;

@@ -19,6 +19,7 @@
 
 #include "zmc_internal.h"
 #include "zmc_runtime.h"
+#include "zmc_trace.h"
 
 namespace zmc {
 
@@ -54,6 +55,7 @@ int fail(int status, const char* fmt, ...) {
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_last_error = buf;
+  log_msg(1, "status %d: %s", status, buf);
   return status;
 }
 
@@ -70,7 +72,9 @@ const char* last_error() { return g_last_error.c_str(); }
 struct DeviceState {
   bool init = false;
   cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;  // device->host copies of chunked scans
   cudaDeviceProp prop{};
+  unsigned long long* dbg = nullptr;   // check words (ZMC_DEBUG builds)
 };
 
 static std::mutex g_mu;
@@ -88,6 +92,13 @@ int device_state(DeviceState** out) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
     e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+    e = cudaStreamCreateWithFlags(&s.copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+#if ZMC_DEBUG
+    e = cudaMalloc(reinterpret_cast<void**>(&s.dbg), 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s.dbg, 0, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(e, "debug check words");
+#endif
     // Keep freed stream-ordered allocations in the pool for reuse.
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
@@ -98,6 +109,38 @@ int device_state(DeviceState** out) {
   }
   *out = &s;
   return ZMC_OK;
+}
+
+unsigned long long* debug_words() {
+#if ZMC_DEBUG
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_dev[dev].init ? g_dev[dev].dbg : nullptr;
+#else
+  return nullptr;
+#endif
+}
+
+int64_t debug_take(unsigned* code, long long* index) {
+#if ZMC_DEBUG
+  unsigned long long* w = debug_words();
+  if (!w) return 0;
+  unsigned long long h[3] = {0, 0, 0};
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(w, 0, sizeof(h)) != cudaSuccess)
+    return 0;
+  if (code) *code = static_cast<unsigned>(h[0]);
+  if (index) *index = static_cast<long long>(h[1]);
+  if (h[2]) log_msg(1, "device-side check %u failed %llu times (first index %lld)",
+                    static_cast<unsigned>(h[0]), h[2], static_cast<long long>(h[1]));
+  return static_cast<int64_t>(h[2]);
+#else
+  (void)code;
+  (void)index;
+  return -1;
+#endif
 }
 
 // ------------------------------------------------------------ validation --
@@ -171,6 +214,8 @@ int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out) {
                   d->tile_lanes);
   }
   if (d->tile_splits < 0) return fail(ZMC_EINVAL, "tile_splits %d < 0", d->tile_splits);
+  if (d->chunk_points < 0)
+    return fail(ZMC_EINVAL, "chunk_points %lld < 0", (long long)d->chunk_points);
   if (P_out) *P_out = P;
   if (count_out) *count_out = count;
   return ZMC_OK;
@@ -210,18 +255,43 @@ TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count,
 
 static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// ------------------------------------------------------------- chunking --
+// zmc_scan_ex cuts a slice into chunks of consecutive grid points (the batches
+// of Sec. 2), so that its device scratch stays bounded whatever the grid size:
+// one chunk of FP64 partial sums (at most kChunkUnitSplits unit-splits,
+// 256 MiB) and, with host buffers, two chunks of outputs whose device->host
+// copies overlap the next chunk's sampling.  Every chunk runs the tile plan
+// of the whole call, so the results do not depend on the chunking.
+constexpr int64_t kChunkUnitSplits = int64_t(1) << 24;
+constexpr int64_t kHostChunkMinPoints = int64_t(1) << 20;
+constexpr int64_t kHostChunks = 8;
+
+int64_t chunk_points_for(const zmc_scan_desc* d, int64_t count, const TilePlan& tp) {
+  if (count <= 0) return 1;
+  if (d->chunk_points > 0) return std::min<int64_t>(d->chunk_points, count);
+  const int64_t per_point = std::max<int64_t>(1, int64_t(d->trials) * tp.splits);
+  int64_t cp = std::max<int64_t>(1, kChunkUnitSplits / per_point);
+  if (d->mem == ZMC_MEM_HOST)
+    cp = std::min(cp, std::max(kHostChunkMinPoints, (count + kHostChunks - 1) / kHostChunks));
+  return std::min(cp, count);
+}
+
 ScanLayout layout_for(const zmc_scan_desc* d, int64_t count, const TilePlan& tp) {
   ScanLayout L{};
   int64_t nvals = 0;
   for (int i = 0; i < d->M; ++i) nvals += d->list_len[i];
+  const int64_t cp = chunk_points_for(d, count, tp);
+  L.chunk_points = cp;
+  L.chunks = count > 0 ? (count + cp - 1) / cp : 0;
+  L.nbuf = L.chunks > 1 ? 2 : 1;
   L.partial = 0;
-  L.partial_bytes = static_cast<size_t>(count) * d->trials * tp.splits * 2 * sizeof(double);
+  L.partial_bytes = static_cast<size_t>(cp) * d->trials * tp.splits * 2 * sizeof(double);
   size_t off = align256(std::max<size_t>(L.partial_bytes, 16));
   L.vals = L.mean = L.err = L.errw = L.s1 = L.s2 = SIZE_MAX;
   if (d->mem == ZMC_MEM_HOST) {
     L.vals = off;
     off = align256(off + static_cast<size_t>(nvals) * sizeof(double));
-    const size_t pb = static_cast<size_t>(std::max<int64_t>(count, 1)) * sizeof(double);
+    const size_t pb = static_cast<size_t>(L.nbuf) * cp * sizeof(double);
     const size_t tb = pb * d->trials;
     L.mean = off; off = align256(off + pb);
     L.err = off;  off = align256(off + pb);
@@ -231,6 +301,31 @@ ScanLayout layout_for(const zmc_scan_desc* d, int64_t count, const TilePlan& tp)
   }
   L.total = off;
   return L;
+}
+
+TilePlan plan_with(const zmc_scan_desc* d, int64_t count, int sm, int tps) {
+  // A class entry recorded by the autotuner, when the caller leaves tiles open.
+  int tl = 0, tb = 0, tg = 0;
+  if (!d->tile_lanes && !d->tile_splits && !d->tile_block &&
+      tune_find(d->precision, d->integrand_id, d->N, d->samples_per_point, &tl, &tb, &tg)) {
+    TilePlan tp;
+    const int G = group_samples(d->N);
+    const int64_t Q = (d->samples_per_point + G - 1) / G;
+    int64_t splits = std::max<int64_t>(1, (Q + int64_t(tl) * tg - 1) / (int64_t(tl) * tg));
+    // small grids: enough ranges for ~4 waves of resident threads
+    const int64_t units = std::max<int64_t>(1, count * d->trials);
+    const int64_t want = int64_t(4) * std::max(1, sm) * std::max(256, tps);
+    if (units * splits * tl < want) {
+      const int64_t more = (want + units * tl - 1) / (units * tl);
+      splits = std::max(splits, std::min(more, std::max<int64_t>(1, Q / (int64_t(tl) * 64))));
+    }
+    tp.lanes = tl;
+    tp.block = tb;
+    tp.splits = static_cast<int>(std::min<int64_t>(splits, std::max<int64_t>(1, Q)));
+    return tp;
+  }
+  return plan_tiles(d->N, d->samples_per_point, d->trials, count, sm, tps, d->tile_lanes,
+                    d->tile_splits, d->tile_block);
 }
 
 int plan_for(const zmc_scan_desc* d, int64_t count, TilePlan* tp) {
@@ -243,29 +338,8 @@ int plan_for(const zmc_scan_desc* d, int64_t count, TilePlan* tp) {
     sm = ds->prop.multiProcessorCount;
     tps = ds->prop.maxThreadsPerMultiProcessor;
   }
-  // A class entry recorded by the autotuner, when the caller leaves tiles open.
-  int tl = 0, tb = 0, tg = 0;
-  if (!d->tile_lanes && !d->tile_splits && !d->tile_block) {
-    tune_ensure_loaded();
-    if (tune_find(d->precision, d->integrand_id, d->N, d->samples_per_point, &tl, &tb, &tg)) {
-      const int G = group_samples(d->N);
-      const int64_t Q = (d->samples_per_point + G - 1) / G;
-      int64_t splits = std::max<int64_t>(1, (Q + int64_t(tl) * tg - 1) / (int64_t(tl) * tg));
-      // small grids: enough ranges for ~4 waves of resident threads
-      const int64_t units = std::max<int64_t>(1, count * d->trials);
-      const int64_t want = int64_t(4) * std::max(1, sm) * std::max(256, tps);
-      if (units * splits * tl < want) {
-        const int64_t more = (want + units * tl - 1) / (units * tl);
-        splits = std::max(splits, std::min(more, std::max<int64_t>(1, Q / (int64_t(tl) * 64))));
-      }
-      tp->lanes = tl;
-      tp->block = tb;
-      tp->splits = static_cast<int>(std::min<int64_t>(splits, std::max<int64_t>(1, Q)));
-      return ZMC_OK;
-    }
-  }
-  *tp = plan_tiles(d->N, d->samples_per_point, d->trials, count, sm, tps, d->tile_lanes,
-                   d->tile_splits, d->tile_block);
+  if (!d->tile_lanes && !d->tile_splits && !d->tile_block) tune_ensure_loaded();
+  *tp = plan_with(d, count, sm, tps);
   return ZMC_OK;
 }
 
@@ -316,6 +390,7 @@ void fill_scan_args(const zmc_scan_desc* d, int64_t count, const TilePlan& tp,
   }
   fill_round_keys(d->seed, a->rk0, a->rk1);
   a->partial = partial_dev;
+  a->dbg = debug_words();
   a->gid = d->integrand_id;
   a->N = d->N;
 }
@@ -342,10 +417,12 @@ int launch_scan_args(const zmc_scan_desc* d, const ScanArgs& a, const TilePlan& 
 }
 
 // -------------------------------------------------------------- the scan --
+// CUDA events of one call (ZMC_F_TIMINGS only; otherwise every call is a no-op).
 struct EventSet {
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> ev;
   bool on = false;
-  int create() {
+  int create(size_t n) {
+    ev.assign(n, nullptr);
     for (auto& e : ev) {
       cudaError_t r = cudaEventCreate(&e);
       if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
@@ -353,10 +430,10 @@ struct EventSet {
     on = true;
     return ZMC_OK;
   }
-  void record(int i, cudaStream_t s) {
+  void record(size_t i, cudaStream_t s) {
     if (on) cudaEventRecord(ev[i], s);
   }
-  float ms(int a, int b) {
+  float ms(size_t a, size_t b) {
     float v = 0.0f;
     if (on) cudaEventElapsedTime(&v, ev[a], ev[b]);
     return v;
@@ -376,7 +453,73 @@ static bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Host memory that the GPU can copy into asynchronously (page-locked, from
+// cudaMallocHost / cudaHostAlloc / cudaHostRegister), first and last byte.
+static bool is_pinned_host(const void* p, size_t bytes) {
+  if (!p || bytes == 0) return true;
+  auto pinned = [](const void* q) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+  };
+  return pinned(p) && pinned(static_cast<const char*>(p) + bytes - 1);
+}
+
+// Page-locked staging buffers for chunked scans into pageable host arrays,
+// kept for reuse across calls (a process-wide free list; each call holds its
+// buffer for its duration, so concurrent calls never share one).
+struct PinnedBuf {
+  char* p = nullptr;
+  size_t bytes = 0;
+};
+static std::mutex g_pin_mu;
+static std::vector<PinnedBuf> g_pin_free;
+
+static int pinned_take(size_t bytes, PinnedBuf* out) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (size_t i = 0; i < g_pin_free.size(); ++i)
+      if (g_pin_free[i].bytes >= bytes) {
+        *out = g_pin_free[i];
+        g_pin_free.erase(g_pin_free.begin() + static_cast<long>(i));
+        return ZMC_OK;
+      }
+  }
+  PinnedBuf b;
+  cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&b.p), bytes, cudaHostAllocDefault);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(staging)");
+  b.bytes = bytes;
+  *out = b;
+  return ZMC_OK;
+}
+
+static void pinned_give(PinnedBuf b) {
+  if (!b.p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(b);
+  if (g_pin_free.size() > 4) {  // keep the four largest
+    auto it = std::min_element(g_pin_free.begin(), g_pin_free.end(),
+                               [](const PinnedBuf& x, const PinnedBuf& y) {
+                                 return x.bytes < y.bytes;
+                               });
+    cudaFreeHost(it->p);
+    g_pin_free.erase(it);
+  }
+}
+
+// One output array of a chunk: where the finalize kernel wrote it on the
+// device, where it goes on the host, and its length in doubles.
+struct OutCopy {
+  double* dst;
+  const double* src;
+  size_t n;
+};
+
 int scan_ex(const zmc_scan_desc* d, zmc_scan_out* o) {
+  TraceRange trace("zmc_scan_ex");
   int64_t P = 0, count = 0;
   int rc = validate(d, &P, &count);
   if (rc != ZMC_OK) return rc;
@@ -405,9 +548,15 @@ int scan_ex(const zmc_scan_desc* d, zmc_scan_out* o) {
   o->tile_lanes = tp.lanes;
   o->tile_splits = tp.splits;
   o->tile_block = tp.block;
+  o->chunks = L.chunks;
   o->launches = 0;
   o->h2d_ms = o->kernel_ms = o->finalize_ms = o->d2h_ms = o->total_ms = 0.0f;
-  if (count == 0 || (d->flags & ZMC_F_PLAN_ONLY)) return ZMC_OK;
+  log_msg(2, "scan: integrand %d N %d precision %d, points [%lld, +%lld) x %d trials x %lld "
+          "samples; tiles lanes %d splits %d block %d; %lld chunk(s) of %lld points; %s memory",
+          d->integrand_id, d->N, d->precision, (long long)d->first_index, (long long)count,
+          d->trials, (long long)d->samples_per_point, tp.lanes, tp.splits, tp.block,
+          (long long)L.chunks, (long long)L.chunk_points, d->mem == ZMC_MEM_HOST ? "host" : "device");
+  if (count == 0 || plan_only) return ZMC_OK;
 
   // Scratch: the caller's workspace or the stream-ordered pool.
   char* ws = static_cast<char*>(d->workspace);
@@ -421,27 +570,62 @@ int scan_ex(const zmc_scan_desc* d, zmc_scan_out* o) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(workspace)");
     own_ws = true;
   }
+
+  const bool host = d->mem == ZMC_MEM_HOST;
+  const int64_t nch = L.chunks, cp = L.chunk_points, T = d->trials;
+  // Several chunks with host buffers: results leave on the copy stream while
+  // the next chunk samples, straight into the caller's arrays when they are
+  // pinned, else through two pinned staging buffers.
+  const bool piped = host && nch > 1;
+  cudaStream_t cs = ds->copy_stream;
+  bool direct = true;
+  const size_t pb_all = static_cast<size_t>(count) * sizeof(double);
+  if (piped)
+    direct = is_pinned_host(o->mean, pb_all) && is_pinned_host(o->err, pb_all) &&
+             is_pinned_host(o->errw, pb_all) && is_pinned_host(o->s1, pb_all * T) &&
+             is_pinned_host(o->s2, pb_all * T);
+  const size_t per_chunk_doubles =
+      static_cast<size_t>(cp) * (2 + (o->errw ? 1 : 0) + (o->s1 ? T : 0) + (o->s2 ? T : 0));
+  PinnedBuf stage;
+  cudaEvent_t ready[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+  bool copies_enqueued = false;
   auto release = [&]() {
+    if (copies_enqueued) cudaStreamSynchronize(cs);
+    for (int b = 0; b < 2; ++b) {
+      if (ready[b]) cudaEventDestroy(ready[b]);
+      if (copied[b]) cudaEventDestroy(copied[b]);
+    }
+    pinned_give(stage);
     if (own_ws) cudaFreeAsync(ws, stream);
   };
+  if (piped) {
+    for (int b = 0; b < 2; ++b) {
+      cudaError_t e = cudaEventCreateWithFlags(&ready[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "cudaEventCreate");
+      }
+    }
+    if (!direct && (rc = pinned_take(2 * per_chunk_doubles * sizeof(double), &stage)) != ZMC_OK) {
+      release();
+      return rc;
+    }
+  }
 
+  // Events: 0 start, 1 lists copied, then per chunk (sampling start, sampling
+  // end, finalize end), then one after the last copy.
   EventSet ev;
   const bool timed = (d->flags & ZMC_F_TIMINGS) != 0;
-  if (timed && (rc = ev.create()) != ZMC_OK) {
+  if (timed && (rc = ev.create(3 + 3 * static_cast<size_t>(nch))) != ZMC_OK) {
     release();
     return rc;
   }
+  const size_t ev_last = 2 + 3 * static_cast<size_t>(nch);
 
-  const bool host = d->mem == ZMC_MEM_HOST;
   const double* vals_dev = d->list_vals;
-  double* mean_dev = o->mean;
-  double* err_dev = o->err;
-  double* errw_dev = o->errw;
-  double* s1_dev = o->s1;
-  double* s2_dev = o->s2;
   int64_t nvals = 0;
   for (int i = 0; i < d->M; ++i) nvals += d->list_len[i];
-
   ev.record(0, stream);
   if (host) {
     double* v = reinterpret_cast<double*>(ws + L.vals);
@@ -452,71 +636,164 @@ int scan_ex(const zmc_scan_desc* d, zmc_scan_out* o) {
       return cuda_fail(e, "cudaMemcpyAsync(lists)");
     }
     vals_dev = v;
-    mean_dev = reinterpret_cast<double*>(ws + L.mean);
-    err_dev = reinterpret_cast<double*>(ws + L.err);
-    errw_dev = o->errw ? reinterpret_cast<double*>(ws + L.errw) : nullptr;
-    s1_dev = o->s1 ? reinterpret_cast<double*>(ws + L.s1) : nullptr;
-    s2_dev = o->s2 ? reinterpret_cast<double*>(ws + L.s2) : nullptr;
   }
   ev.record(1, stream);
 
-  ScanArgs a;
-  fill_scan_args(d, count, tp, vals_dev, reinterpret_cast<double*>(ws + L.partial), &a);
-  rc = launch_scan_args(d, a, tp, stream);
-  if (rc != ZMC_OK) {
-    release();
-    return rc;
-  }
-  ev.record(2, stream);
-
-  FinalizeArgs f;
-  f.count = count;
-  f.S = d->samples_per_point;
-  f.T = d->trials;
-  f.splits = tp.splits;
-  f.V = box_volume(d);
-  f.partial = a.partial;
-  f.mean = mean_dev;
-  f.err = err_dev;
-  f.errw = errw_dev;
-  f.s1 = s1_dev;
-  f.s2 = s2_dev;
-  int e2 = finalize_launch(f, stream);
-  if (e2 != 0) {
-    release();
-    return cuda_fail(static_cast<cudaError_t>(e2), "finalize kernel launch");
-  }
-  o->launches = 2;
-  ev.record(3, stream);
-
-  if (host) {
-    const size_t pb = static_cast<size_t>(count) * sizeof(double);
-    const size_t tb = pb * d->trials;
-    struct Cp { void* dst; const void* src; size_t n; } cps[5] = {
-        {o->mean, mean_dev, pb}, {o->err, err_dev, pb}, {o->errw, errw_dev, pb},
-        {o->s1, s1_dev, tb}, {o->s2, s2_dev, tb}};
+  // The outputs of chunk k (points [k cp, k cp + n) of the slice): on the
+  // device (finalize's targets) and their host destinations.
+  auto chunk_outputs = [&](int64_t k, int64_t n, int b, double* dev[5], OutCopy cps[5]) {
+    const int64_t off = k * cp;
+    if (!host) {
+      dev[0] = o->mean + off;
+      dev[1] = o->err + off;
+      dev[2] = o->errw ? o->errw + off : nullptr;
+      dev[3] = o->s1 ? o->s1 + off * T : nullptr;
+      dev[4] = o->s2 ? o->s2 + off * T : nullptr;
+      return;
+    }
+    const size_t bo = static_cast<size_t>(b) * cp;
+    dev[0] = reinterpret_cast<double*>(ws + L.mean) + bo;
+    dev[1] = reinterpret_cast<double*>(ws + L.err) + bo;
+    dev[2] = o->errw ? reinterpret_cast<double*>(ws + L.errw) + bo : nullptr;
+    dev[3] = o->s1 ? reinterpret_cast<double*>(ws + L.s1) + bo * T : nullptr;
+    dev[4] = o->s2 ? reinterpret_cast<double*>(ws + L.s2) + bo * T : nullptr;
+    double* hdst[5] = {o->mean + off, o->err + off, o->errw ? o->errw + off : nullptr,
+                       o->s1 ? o->s1 + off * T : nullptr, o->s2 ? o->s2 + off * T : nullptr};
+    const size_t len[5] = {size_t(n), size_t(n), size_t(n), size_t(n * T), size_t(n * T)};
+    for (int i = 0; i < 5; ++i) cps[i] = {hdst[i], dev[i], hdst[i] ? len[i] : 0};
+  };
+  // Chunk k's outputs, copied by the GPU into staging buffer b, go to the
+  // caller's pageable arrays.
+  auto unstage = [&](int64_t k, int b) {
+    const int64_t n = std::min(cp, count - k * cp);
+    double* dev[5];
+    OutCopy cps[5];
+    chunk_outputs(k, n, b, dev, cps);
+    const double* src = reinterpret_cast<const double*>(stage.p) + b * per_chunk_doubles;
     for (auto& c : cps) {
-      if (!c.dst) continue;
-      cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyDeviceToHost, stream);
+      if (!c.n) continue;
+      std::memcpy(c.dst, src, c.n * sizeof(double));
+      src += c.n;
+    }
+  };
+
+  const double V = box_volume(d);
+  for (int64_t k = 0; k < nch; ++k) {
+    TraceRange chunk_trace("zmc_scan_ex chunk");
+    const int64_t n = std::min(cp, count - k * cp);
+    const int b = piped ? static_cast<int>(k & 1) : 0;
+    log_msg(3, "chunk %lld/%lld: points [%lld, +%lld)%s", (long long)k, (long long)nch,
+            (long long)(d->first_index + k * cp), (long long)n,
+            piped ? (direct ? ", copied straight to pinned host arrays"
+                            : ", copied through pinned staging") : "");
+    zmc_scan_desc dc = *d;
+    dc.first_index = d->first_index + k * cp;
+    dc.count = n;
+    ScanArgs a;
+    fill_scan_args(&dc, n, tp, vals_dev, reinterpret_cast<double*>(ws + L.partial), &a);
+    ev.record(2 + 3 * k, stream);
+    rc = launch_scan_args(d, a, tp, stream);
+    if (rc != ZMC_OK) {
+      release();
+      return rc;
+    }
+    ev.record(3 + 3 * k, stream);
+    // output buffer b was last read by the copy of chunk k - 2
+    if (piped && k >= 2) cudaStreamWaitEvent(stream, copied[b], 0);
+    double* dev[5];
+    OutCopy cps[5];
+    chunk_outputs(k, n, b, dev, cps);
+    FinalizeArgs f;
+    f.count = n;
+    f.S = d->samples_per_point;
+    f.T = d->trials;
+    f.splits = tp.splits;
+    f.V = V;
+    f.partial = a.partial;
+    f.mean = dev[0];
+    f.err = dev[1];
+    f.errw = dev[2];
+    f.s1 = dev[3];
+    f.s2 = dev[4];
+    int e2 = finalize_launch(f, stream);
+    if (e2 != 0) {
+      release();
+      return cuda_fail(static_cast<cudaError_t>(e2), "finalize kernel launch");
+    }
+    o->launches += 2;
+    ev.record(4 + 3 * k, stream);
+    if (!host) continue;
+    cudaStream_t cstream = piped ? cs : stream;
+    if (piped) {
+      cudaEventRecord(ready[b], stream);
+      cudaStreamWaitEvent(cs, ready[b], 0);
+    }
+    double* sdst = piped && !direct
+                       ? reinterpret_cast<double*>(stage.p) + b * per_chunk_doubles
+                       : nullptr;
+    for (auto& c : cps) {
+      if (!c.n) continue;
+      double* dst = sdst ? sdst : c.dst;
+      cudaError_t e = cudaMemcpyAsync(dst, c.src, c.n * sizeof(double),
+                                      cudaMemcpyDeviceToHost, cstream);
       if (e != cudaSuccess) {
         release();
         return cuda_fail(e, "cudaMemcpyAsync(results)");
       }
+      copies_enqueued = copies_enqueued || piped;
+      if (sdst) sdst += c.n;
+    }
+    if (piped) {
+      cudaEventRecord(copied[b], cs);
+      // the previous chunk's staged results to the caller while this chunk runs
+      if (!direct && k >= 1) {
+        cudaError_t e = cudaEventSynchronize(copied[b ^ 1]);
+        if (e != cudaSuccess) {
+          release();
+          return cuda_fail(e, "cudaEventSynchronize(chunk copy)");
+        }
+        unstage(k - 1, b ^ 1);
+      }
     }
   }
-  ev.record(4, stream);
+  if (piped) {
+    const int bl = static_cast<int>((nch - 1) & 1);
+    if (!direct) {
+      cudaError_t e = cudaEventSynchronize(copied[bl]);
+      if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "cudaEventSynchronize(chunk copy)");
+      }
+      unstage(nch - 1, bl);
+    }
+    cudaStreamWaitEvent(stream, copied[bl], 0);  // the workspace outlives the copies
+    copies_enqueued = false;  // ordered behind the stream: no wait on the copy stream
+  }
+  ev.record(ev_last, stream);
   release();
 
-  if (host || timed || (d->flags & ZMC_F_SYNC)) {
+  if (host || timed || ZMC_DEBUG || (d->flags & ZMC_F_SYNC)) {
     cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   }
+#if ZMC_DEBUG
+  {
+    unsigned code = 0;
+    long long index = 0;
+    const int64_t nfail = debug_take(&code, &index);
+    if (nfail > 0)
+      return fail(ZMC_ECUDA, "device-side check %u failed %lld times (first index %lld)",
+                  code, static_cast<long long>(nfail), index);
+  }
+#endif
   if (timed) {
     o->h2d_ms = ev.ms(0, 1);
-    o->kernel_ms = ev.ms(1, 2);
-    o->finalize_ms = ev.ms(2, 3);
-    o->d2h_ms = ev.ms(3, 4);
-    o->total_ms = ev.ms(0, 4);
+    for (int64_t k = 0; k < nch; ++k) {
+      o->kernel_ms += ev.ms(2 + 3 * k, 3 + 3 * k);
+      o->finalize_ms += ev.ms(3 + 3 * k, 4 + 3 * k);
+    }
+    o->d2h_ms = host ? ev.ms(4 + 3 * (nch - 1), ev_last) : 0.0f;
+    o->total_ms = ev.ms(0, ev_last);
   }
   return ZMC_OK;
 }
@@ -622,6 +899,15 @@ int zmc_scan(int integrand_id, int N, const double* lo, const double* hi, int M,
   o.mean = out_mean;
   o.err = out_err;
   return scan_ex(&d, &o);
+}
+
+int64_t zmc_debug_failures(unsigned* code, long long* index) {
+  unsigned c = 0;
+  long long i = 0;
+  const int64_t n = debug_take(&c, &i);
+  if (code) *code = c;
+  if (index) *index = i;
+  return n;
 }
 
 int zmc_stream_words(uint64_t seed, int64_t p, int t, uint64_t first_word, int64_t nwords,

@@ -170,7 +170,9 @@ __device__ __forceinline__ void load_params(const ScanArgs& a, const void* table
 #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
       const int64_t d = next_digit(a, p, a.len[i]);
-      const int idx = a.off[i] + static_cast<int>(d);
+      int idx = a.off[i] + static_cast<int>(d);
+      if (!ZMC_CHECK(a.dbg, d >= 0 && d < a.len[i] && idx < a.nvals, kDbgListOffset, idx))
+        idx = 0;
       const float2 v = table ? static_cast<const float2*>(table)[idx]
                              : F::value(i, a.vals[idx], a.lo[i], a.hi[i]);
       f.load(i, v, &dimc[3 * i]);
@@ -181,7 +183,10 @@ __device__ __forceinline__ void load_params(const ScanArgs& a, const void* table
 #pragma unroll
     for (int i = F::kFixedM - 1; i >= 0; --i) {
       const int64_t d = next_digit(a, p, a.len[i]);
-      f.set_param(i, vals[a.off[i] + d]);
+      int64_t idx = a.off[i] + d;
+      if (!ZMC_CHECK(a.dbg, d >= 0 && d < a.len[i] && idx < a.nvals, kDbgListOffset, idx))
+        idx = 0;
+      f.set_param(i, vals[idx]);
     }
     f.finish(a.lo, a.hi);
   } else if constexpr (F::kPerDim) {
@@ -190,13 +195,19 @@ __device__ __forceinline__ void load_params(const ScanArgs& a, const void* table
 #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
       const int64_t d = next_digit(a, p, a.len[i]);
-      f.set(i, vals[a.off[i] + d], a.lo[i], a.hi[i]);
+      int64_t idx = a.off[i] + d;
+      if (!ZMC_CHECK(a.dbg, d >= 0 && d < a.len[i] && idx < a.nvals, kDbgListOffset, idx))
+        idx = 0;
+      f.set(i, vals[idx], a.lo[i], a.hi[i]);
     }
   } else {
     const double* vals = table ? static_cast<const double*>(table) : a.vals;
     for (int i = a.M - 1; i >= 0; --i) {
       const int64_t d = next_digit(a, p, a.len[i]);
-      f.add(vals[a.off[i] + d]);
+      int64_t idx = a.off[i] + d;
+      if (!ZMC_CHECK(a.dbg, d >= 0 && d < a.len[i] && idx < a.nvals, kDbgListOffset, idx))
+        idx = 0;
+      f.add(vals[idx]);
     }
     f.finish(a.lo, a.hi);
   }
@@ -213,6 +224,9 @@ __device__ __forceinline__ const void* stage_lists(const ScanArgs& a, double* sm
     if (a.stage_smem) {
       float2* tab = reinterpret_cast<float2*>(smem);
       for (int i = threadIdx.x; i < a.nvals; i += blockDim.x) {
+        if (!ZMC_CHECK(a.dbg, (i + 1) * sizeof(float2) <= dynamic_smem_bytes(),
+                       kDbgStagedTable, i))
+          break;
         const int k = list_of(a, i);
         tab[i] = F::value(k, a.vals[i], a.lo[k], a.hi[k]);
       }
@@ -221,7 +235,12 @@ __device__ __forceinline__ const void* stage_lists(const ScanArgs& a, double* sm
     return a.stage_smem ? smem : nullptr;
   } else {
     if (a.stage_smem) {
-      for (int i = threadIdx.x; i < a.nvals; i += blockDim.x) smem[i] = a.vals[i];
+      for (int i = threadIdx.x; i < a.nvals; i += blockDim.x) {
+        if (!ZMC_CHECK(a.dbg, (i + 1) * sizeof(double) <= dynamic_smem_bytes(),
+                       kDbgStagedTable, i))
+          break;
+        smem[i] = a.vals[i];
+      }
       __syncthreads();
       return smem;
     }
@@ -390,6 +409,8 @@ __device__ __forceinline__ void unit_split_lane(const ScanArgs& a, const uint32_
   const int64_t lp = unit / a.T;
   const uint32_t t = static_cast<uint32_t>(unit - lp * a.T);
   const int64_t p = a.first + lp;
+  if (!ZMC_CHECK(a.dbg, us >= 0 && lp < a.count && split < a.splits, kDbgGridIndex, us))
+    return;
 
   F f{};
   load_params<N>(a, table, dimc, p, f);
@@ -464,7 +485,7 @@ scan_kernel(const __grid_constant__ ScanArgs a) {
   if (us < a.n_us) unit_split_lane<N, F, PREC>(a, a.rk0, a.rk1, table, dimc, us, lane, acc);
   double s1 = acc.sum1(), s2 = acc.sum2();
   reduce_unit_split(a, s1, s2, red);
-  if (lane == 0 && us < a.n_us) {
+  if (lane == 0 && us < a.n_us && ZMC_CHECK(a.dbg, us >= 0, kDbgPartialSlot, us)) {
     a.partial[2 * us] = s1;
     a.partial[2 * us + 1] = s2;
   }

@@ -9,10 +9,15 @@
 //   3. upload the step's scan arguments and tiles, launch one persistent
 //      sampling kernel per precision, then one batched finalize for every
 //      chunk whose last tiles are in this step;
-//   4. while the step runs, copy the previous step's finished chunks to the
-//      callers' host buffers on a second stream;
-//   5. wait for the step; chunks finished by it are copied during the next
-//      step; a request is done when its last chunk is in host memory.
+//   4. while the step runs, hand the previous step's finished chunks to the
+//      copier thread, which copies them into the callers' host arrays on a
+//      second stream (a copy into pageable memory holds the calling thread
+//      until it is done, so it never runs on the scheduler thread);
+//   5. wait for the step; a request is done when the copier has put its last
+//      chunk in host memory.
+// A chunk's output buffer on the device is finalized into again only after
+// the copier has copied its previous contents out (the scheduler does not
+// pick the tiles that would complete a chunk while its buffer is busy).
 // No kernel waits on anything; every host wait is on a CUDA event of work
 // already enqueued, or a condition variable with a deadline.
 #include <cuda_runtime.h>
@@ -33,6 +38,7 @@
 #include "../../include/zmc_server.h"
 #include "zmc_internal.h"
 #include "zmc_runtime.h"
+#include "zmc_trace.h"
 
 namespace zmc {
 
@@ -64,14 +70,20 @@ struct Request {
   double* d_part = nullptr;
   double* d_out[2] = {nullptr, nullptr};
   size_t out_doubles = 0;  // per buffer
-  cudaEvent_t copied[2] = {nullptr, nullptr};
-  bool copy_pending[2] = {false, false};
+  // copier thread state: d_out[b] is being copied out; chunks in the
+  // caller's host arrays; copy jobs queued or running; a failed copy
+  std::atomic<bool> buf_busy[2];
+  std::atomic<int64_t> delivered{0};
+  std::atomic<int> jobs{0};
+  std::atomic<int> copy_status{ZMC_OK};
   // progress of the current chunk
   int64_t chunk = 0, chunk_first = 0, chunk_count = 0;
   int64_t chunk_units = 0, chunk_tiles = 0, next_tile = 0;
   ScanArgs args{};
-  bool awaiting_last_copy = false;  // every tile of the last chunk is launched
-  bool last_copy_issued = false;    // ... and its device->host copy is enqueued
+  Request() {
+    buf_busy[0].store(false);
+    buf_busy[1].store(false);
+  }
   // shared with API threads (under the server mutex)
   int status = ZMC_OK;
   bool done = false;
@@ -97,6 +109,13 @@ struct zmc_server {
   uint64_t next_id = 1;
   bool stop = false;
   std::thread thread;
+  uint64_t wake = 0;  // bumped by the copier when a copy job ends (under mu)
+  // copier thread: device->host copies of finished chunks, in order
+  std::thread copier;
+  std::mutex cmu;
+  std::condition_variable ccv;
+  std::deque<zmc::ChunkDone> cjobs;
+  bool cstop = false;
   // scheduler-owned
   std::vector<std::shared_ptr<zmc::Request>> active;
   int64_t seq = 0;
@@ -154,11 +173,6 @@ static void finish_request(zmc_server* s, const std::shared_ptr<Request>& r, int
 }
 
 static void release_device(zmc_server* s, Request* r) {
-  for (int b = 0; b < 2; ++b)
-    if (r->copied[b]) {
-      cudaEventDestroy(r->copied[b]);
-      r->copied[b] = nullptr;
-    }
   if (r->dev) {
     cudaFreeAsync(r->dev, s->compute);
     r->dev = nullptr;
@@ -207,7 +221,6 @@ static int admit_one(zmc_server* s, const std::shared_ptr<Request>& r) {
   for (int b = 0; b < nbuf; ++b) {
     r->d_out[b] = reinterpret_cast<double*>(r->dev + off);
     off = s256(off + r->out_doubles * sizeof(double));
-    cudaEventCreateWithFlags(&r->copied[b], cudaEventDisableTiming);
   }
   e = cudaMemcpyAsync(r->d_vals, r->vals.data(), r->vals.size() * sizeof(double),
                       cudaMemcpyHostToDevice, s->compute);
@@ -217,8 +230,10 @@ static int admit_one(zmc_server* s, const std::shared_ptr<Request>& r) {
   return ZMC_OK;
 }
 
-// Enqueue the device->host copies of a finished chunk on the copy stream.
-static int copy_chunk(zmc_server* s, const ChunkDone& c) {
+// Copy a finished chunk (its finalize has completed) from its device output
+// buffer into the caller's host arrays.  Runs on the copier thread: a copy
+// into pageable memory returns only when it is done.
+static int copy_chunk_now(zmc_server* s, const ChunkDone& c) {
   Request* r = c.r.get();
   const int64_t off = c.first - r->d.first_index;
   const int64_t n = c.count, T = r->d.trials;
@@ -235,9 +250,53 @@ static int copy_chunk(zmc_server* s, const ChunkDone& c) {
                                     cudaMemcpyDeviceToHost, s->copy);
     if (e != cudaSuccess) return ZMC_ECUDA;
   }
-  cudaEventRecord(r->copied[c.buf], s->copy);
-  r->copy_pending[c.buf] = true;
-  return ZMC_OK;
+  return cudaStreamSynchronize(s->copy) == cudaSuccess ? ZMC_OK : ZMC_ECUDA;
+}
+
+static void copier_loop(zmc_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    ChunkDone c;
+    {
+      std::unique_lock<std::mutex> lk(s->cmu);
+      s->ccv.wait(lk, [&] { return s->cstop || !s->cjobs.empty(); });
+      if (s->cjobs.empty()) return;
+      c = s->cjobs.front();
+      s->cjobs.pop_front();
+    }
+    Request* r = c.r.get();
+    if (!r->cancel.load()) {
+      if (copy_chunk_now(s, c) == ZMC_OK)
+        r->delivered.fetch_add(1);
+      else
+        r->copy_status.store(ZMC_ECUDA);
+    }
+    r->buf_busy[c.buf].store(false);
+    r->jobs.fetch_sub(1);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->wake++;
+    }
+    s->cv_work.notify_one();
+  }
+}
+
+// Hand a finished chunk to the copier thread.
+static void copy_chunk(zmc_server* s, const ChunkDone& c) {
+  Request* r = c.r.get();
+  r->buf_busy[c.buf].store(true);
+  r->jobs.fetch_add(1);
+  {
+    std::lock_guard<std::mutex> lk(s->cmu);
+    s->cjobs.push_back(c);
+  }
+  s->ccv.notify_one();
+}
+
+// Wait until the copier has no job of r queued or running (it skips the
+// jobs of cancelled requests, and a running copy ends by itself).
+static void drain_jobs(Request* r) {
+  while (r->jobs.load() > 0) std::this_thread::sleep_for(std::chrono::microseconds(50));
 }
 
 struct StepPick {
@@ -268,11 +327,7 @@ static void retire_step(zmc_server* s, Step& st) {
   for (auto& c : st.completing) {
     Request* r = c.r.get();
     if (r->done || r->cancel.load()) continue;
-    if (copy_chunk(s, c) != ZMC_OK) {
-      r->cancel.store(true);
-      continue;
-    }
-    if (c.chunk == r->nchunks - 1) r->last_copy_issued = true;
+    copy_chunk(s, c);
   }
 }
 
@@ -294,6 +349,10 @@ static void run_loop(zmc_server* s) {
         s->cv_work.wait_for(lk, std::chrono::milliseconds(50));
       stopping = s->stop;
     }
+    const uint64_t wake_seen = [&] {
+      std::lock_guard<std::mutex> lk(s->mu);
+      return s->wake;
+    }();
     // cancelled or stopping: queued requests end now
     {
       std::vector<std::shared_ptr<Request>> ended;
@@ -327,6 +386,9 @@ static void run_loop(zmc_server* s) {
         release_device(s, r.get());
         finish_request(s, r, rc);
       } else {
+        log_msg(2, "server: admitted request %llu (integrand %d N %d, %lld points in %lld "
+                "chunk(s), %zu device bytes)", (unsigned long long)r->id, r->d.integrand_id,
+                r->d.N, (long long)r->count, (long long)r->nchunks, r->bytes);
         s->active.push_back(r);
       }
     }
@@ -335,7 +397,6 @@ static void run_loop(zmc_server* s) {
         retire_step(s, inflight.front());
         inflight.pop_front();
       }
-      cudaStreamSynchronize(s->copy);
       return;
     }
     // 2. pick tiles (skip cancelled requests and those with every tile launched)
@@ -371,6 +432,10 @@ static void run_loop(zmc_server* s) {
         int64_t k = static_cast<int64_t>(allot / tile_evals);
         k = std::max<int64_t>(1, std::min(k, r->chunk_tiles - r->next_tile));
         k = std::min(k, s->tile_cap - tiles_used);
+        // the chunk's output buffer still holds an earlier chunk being copied
+        // out: run all but its last tile now, finalize it in a later step
+        if (r->next_tile + k == r->chunk_tiles && r->buf_busy[r->chunk % 2].load()) --k;
+        if (k <= 0) continue;
         StepPick p{ready[i], r->next_tile, r->next_tile + k, r->next_tile + k == r->chunk_tiles};
         r->next_tile += k;
         tiles_used += k;
@@ -382,6 +447,7 @@ static void run_loop(zmc_server* s) {
     }
     // 3. upload and launch the step
     if (!picks.empty()) {
+      TraceRange step_trace("zmc_server step");
       Step st;
       st.slot = slot;
       const int nsc = static_cast<int>(picks.size());
@@ -427,9 +493,6 @@ static void run_loop(zmc_server* s) {
                     per_block * groups * G;
         if (picks[i].completes_chunk) {
           const int buf = static_cast<int>(r->chunk % 2);
-          if (r->copy_pending[buf]) {  // the buffer's previous chunk must be in host memory
-            cudaStreamWaitEvent(s->compute, r->copied[buf], 0);
-          }
           FinalizeArgs f;
           const int64_t n = r->chunk_count, T = r->d.trials;
           double* base = r->d_out[buf];
@@ -444,6 +507,7 @@ static void run_loop(zmc_server* s) {
           f.errw = r->o.errw ? base + 2 * n : nullptr;
           f.s1 = r->o.s1 ? base + 3 * n : nullptr;
           f.s2 = r->o.s2 ? base + 3 * n + n * T : nullptr;
+          f.dbg = r->args.dbg;
           fa.push_back(f);
           prefix.push_back(prefix.back() + n);
           st.completing.push_back(ChunkDone{picks[i].r, r->chunk, r->chunk_first, n, buf});
@@ -464,6 +528,8 @@ static void run_loop(zmc_server* s) {
         ba.tiles = reinterpret_cast<const BatchTile*>(s->d_stage + off_tiles) + gbeg[prec];
         ba.ntiles = gend[prec] - gbeg[prec];
         ba.counter = cnt;
+        ba.nscans = nsc;
+        ba.dbg = debug_words();
         int per_sm = 1, sm = 1;
         batch_blocks_per_sm(prec, kServeBlock, gsmem[prec], &per_sm);
         cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, s->device);
@@ -497,11 +563,10 @@ static void run_loop(zmc_server* s) {
         // tiles run after this step's finalize on the same stream
         for (auto& c : st.completing) {
           Request* r = c.r.get();
-          if (c.chunk + 1 < r->nchunks)
-            start_chunk(r, c.chunk + 1);
-          else
-            r->awaiting_last_copy = true;
+          if (c.chunk + 1 < r->nchunks) start_chunk(r, c.chunk + 1);
         }
+        log_msg(3, "server step: %d request(s), %lld tiles, %.3g evaluations, %zu chunk(s) "
+                "finalized", nsc, (long long)nt, st.evals, st.completing.size());
         inflight.push_back(std::move(st));
         slot ^= 1;
       }
@@ -513,22 +578,27 @@ static void run_loop(zmc_server* s) {
     } else if (!inflight.empty()) {
       retire_step(s, inflight.front());
       inflight.pop_front();
-    } else {
-      // nothing to compute: let pending copies finish
-      cudaStreamSynchronize(s->copy);
+    } else if (!s->active.empty()) {
+      // nothing to launch: wait (briefly) for the copier to deliver a chunk
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait_for(lk, std::chrono::milliseconds(5),
+                          [&] { return s->wake != wake_seen || s->stop || !s->queue.empty(); });
     }
-    // 5. requests whose last chunk reached host memory, and cancellations
+    // 5. requests whose last chunk reached host memory, failed copies, and
+    // cancellations (their copy jobs drained first: the copier never writes
+    // into a finished request's arrays or reads its freed buffers)
     std::vector<std::shared_ptr<Request>> keep;
     for (auto& r : s->active) {
-      if (r->cancel.load() || stopping) {
-        cudaStreamSynchronize(s->copy);
+      const int cst = r->copy_status.load();
+      if (r->cancel.load() || stopping || cst != ZMC_OK) {
+        r->cancel.store(true);
+        drain_jobs(r.get());
         cudaStreamSynchronize(s->compute);
         release_device(s, r.get());
-        finish_request(s, r, ZMC_ECANCELED);
+        finish_request(s, r, cst != ZMC_OK ? cst : ZMC_ECANCELED);
         continue;
       }
-      const int last_buf = static_cast<int>((r->nchunks - 1) % 2);
-      if (r->last_copy_issued && cudaEventQuery(r->copied[last_buf]) == cudaSuccess) {
+      if (r->delivered.load() == r->nchunks) {
         release_device(s, r.get());
         finish_request(s, r, ZMC_OK);
         continue;
@@ -599,6 +669,7 @@ int zmc_server_create(size_t mem_budget_bytes, const zmc_server_opts* opts, zmc_
     delete s;
     return rc;
   }
+  s->copier = std::thread(copier_loop, s);
   s->thread = std::thread(run_loop, s);
   *out = s;
   return ZMC_OK;
@@ -756,6 +827,12 @@ int zmc_server_destroy(zmc_server* s) {
     s->cv_work.notify_all();
   }
   if (s->thread.joinable()) s->thread.join();
+  {
+    std::lock_guard<std::mutex> lk(s->cmu);
+    s->cstop = true;
+  }
+  s->ccv.notify_all();
+  if (s->copier.joinable()) s->copier.join();
   cudaStreamSynchronize(s->compute);
   cudaStreamSynchronize(s->copy);
   cudaFree(s->d_counters);

@@ -10,7 +10,8 @@ paper's batches-to-GPUs scheme (Sec. 2) without a task scheduler.
 """
 from __future__ import annotations
 
-from typing import Tuple
+import time
+from typing import Callable, Dict, Tuple
 
 import numpy as np
 
@@ -57,15 +58,37 @@ def barrier():
 
 def gather_slices(local: np.ndarray, P: int) -> np.ndarray:
     """Host-side gather of every rank's slice into the whole grid (all ranks
-    receive it).  `local` holds this rank's shard_range slice."""
+    receive it).  `local` holds this rank's shard_range slice: one value per
+    point, or one row per point (e.g. the per-trial sums)."""
+    local = np.asarray(local)
     dist = _dist()
     if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
-        return np.asarray(local)
+        return local
     world, rank = dist.get_world_size(), dist.get_rank()
     parts = [None] * world
-    dist.all_gather_object(parts, (rank, np.asarray(local)))
-    out = np.empty(P, dtype=np.asarray(local).dtype)
+    dist.all_gather_object(parts, (rank, local))
+    out = np.empty((P,) + local.shape[1:], dtype=local.dtype)
     for r, arr in parts:
         first, count = shard_range(P, r, world)
         out[first:first + count] = arr
     return out
+
+
+def sharded_scan(P: int, scan_slice: Callable[[int, int], Dict[str, np.ndarray]]):
+    """One sharded pass over a grid of P points: this rank runs
+    ``scan_slice(first, count)`` on its shard_range slice between two
+    barriers, the wall time is reduced to the slowest rank, and every output
+    array the function returns (a value or a row per point of the slice) is
+    gathered into the whole grid.  Returns (gathered arrays, slowest rank's
+    seconds)."""
+    dist = _dist()
+    on = dist.is_available() and dist.is_initialized()
+    world = dist.get_world_size() if on else 1
+    rank = dist.get_rank() if on else 0
+    first, count = shard_range(P, rank, world)
+    barrier()
+    t0 = time.perf_counter()
+    local = scan_slice(first, count)
+    barrier()
+    slowest = max_over_ranks(time.perf_counter() - t0)
+    return {k: gather_slices(v, P) for k, v in local.items()}, slowest

@@ -24,6 +24,8 @@ The workloads:
                         box [0,10]^N, S = 10^4
   sinsum_table2         the sine-sum test of Eq. 4 (Sec. 3.2): M = 4, N = 6,
                         lists {0..99}, box [0,1]^6, S = 10^5
+  registry_scan         one scan per (integrand, N) of the registry, ~10^5
+                        points x 4 trials x 2^15 samples (per-kernel sweeps)
 """
 from __future__ import annotations
 
@@ -168,6 +170,38 @@ def sinsum_table2(samples: int = 100_000, trials: int = 1, seed: int = 0) -> Sca
     lists = [np.arange(100.0) for _ in range(4)]
     return ScanSpec("sinsum_table2_M4_N6", G_SINSUM, 6, np.zeros(6), np.ones(6),
                     lists, samples, trials, seed)
+
+
+def registry_scan(gid: int, N: int, points: int = 100_000, samples: int = 1 << 15,
+                  trials: int = 4) -> ScanSpec:
+    """One scan of integrand `gid` at dimension N for per-kernel throughput
+    sweeps: M = N lists, the first min(N, 3) of length round(points^(1/min(N,3)))
+    and the rest of length 1, drawn from default_rng(100 + 10 gid + N).  Boxes
+    and parameter ranges as in the workloads above: cos-product and polynomial
+    on [0,1]^N with x ~ U[0.5, 5]; Gaussian on [-1,1]^N with x ~ U[-1, 1];
+    oscillatory on [0,2]^N with x ~ U[0.5, 5]; sine-sum on [0,1]^N with
+    integer x in {0..99}."""
+    rng = np.random.default_rng(100 + 10 * gid + N)
+    m = min(N, 3)
+    side = max(1, int(round(points ** (1.0 / m))))
+    lens = [side] * m + [1] * (N - m)
+    if gid == G_GAUSS03:
+        lo, hi = -np.ones(N), np.ones(N)
+        lists = [rng.uniform(-1.0, 1.0, L) for L in lens]
+    elif gid == G_OSC01:
+        lo, hi = np.zeros(N), 2.0 * np.ones(N)
+        lists = [rng.uniform(0.5, 5.0, L) for L in lens]
+    elif gid == G_SINSUM:
+        lo, hi = np.zeros(N), np.ones(N)
+        lists = [rng.integers(0, 100, L).astype(np.float64) for L in lens]
+    else:
+        lo, hi = np.zeros(N), np.ones(N)
+        lists = [rng.uniform(0.5, 5.0, L) for L in lens]
+    names = {G_CONST: "const", G_COSPROD: "cosprod", G_GAUSS03: "gauss03", G_POLY: "poly",
+             G_OSC01: "osc01", G_SINSUM: "sinsum"}
+    P = int(np.prod(lens))
+    return ScanSpec("%s_N%d_P%d_S%d_T%d" % (names[gid], N, P, samples, trials), gid, N, lo, hi,
+                    lists, samples, trials, 0)
 
 
 def sample_points(P: int, count: int, seed: int = 12345) -> np.ndarray:

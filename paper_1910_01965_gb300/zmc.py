@@ -15,7 +15,8 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIBRARY = os.path.join(_PKG, "libzmc.so")
+# ZMC_LIBRARY names another build of the library (e.g. libzmc_debug.so).
+LIBRARY = os.environ.get("ZMC_LIBRARY") or os.path.join(_PKG, "libzmc.so")
 
 ZMC_OK, ZMC_EINVAL, ZMC_ENOMEM, ZMC_ECUDA, ZMC_ETIMEDOUT, ZMC_ECANCELED, \
     ZMC_EBUSY, ZMC_ENOTFOUND = range(8)
@@ -52,7 +53,8 @@ class zmc_scan_desc(ctypes.Structure):
                 ("count", ctypes.c_int64), ("stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("tile_lanes", ctypes.c_int), ("tile_splits", ctypes.c_int),
-                ("tile_block", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("tile_block", ctypes.c_int), ("flags", ctypes.c_int),
+                ("chunk_points", ctypes.c_int64)]
 
 
 class zmc_scan_out(ctypes.Structure):
@@ -61,7 +63,7 @@ class zmc_scan_out(ctypes.Structure):
                 ("tile_block", ctypes.c_int), ("launches", ctypes.c_int),
                 ("h2d_ms", ctypes.c_float), ("kernel_ms", ctypes.c_float),
                 ("finalize_ms", ctypes.c_float), ("d2h_ms", ctypes.c_float),
-                ("total_ms", ctypes.c_float)]
+                ("total_ms", ctypes.c_float), ("chunks", ctypes.c_int64)]
 
 
 class zmc_integrand_info(ctypes.Structure):
@@ -170,6 +172,8 @@ SIGNATURES = [
     ("zmc_autotune_reset", ctypes.c_int, []),
     ("zmc_integrand_register", ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int,
                                               ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("zmc_debug_failures", ctypes.c_int64, [ctypes.POINTER(ctypes.c_uint),
+                                            ctypes.POINTER(ctypes.c_longlong)]),
 ]
 
 _lock = threading.Lock()
@@ -207,6 +211,14 @@ def zmc_version() -> int:
 
 def zmc_last_error() -> str:
     return load().zmc_last_error().decode(errors="replace")
+
+
+def zmc_debug_failures():
+    """(failed device-side checks since the last call, first failure's code,
+    its index); failures = -1 in builds without checks."""
+    code, index = ctypes.c_uint(0), ctypes.c_longlong(0)
+    n = load().zmc_debug_failures(ctypes.byref(code), ctypes.byref(index))
+    return int(n), int(code.value), int(index.value)
 
 
 def zmc_scan_desc_init() -> zmc_scan_desc:
@@ -460,7 +472,7 @@ class _Keep:
 
 def make_desc(gid, N, lo, hi, lengths, values=None, S=1, T=1, seed=0,
               precision=ZMC_FP32_KAHAN, mem=ZMC_MEM_HOST, first_index=0, count=-1,
-              stream=None, tiles=(0, 0, 0), flags=0, keep=None):
+              stream=None, tiles=(0, 0, 0), flags=0, keep=None, chunk_points=0):
     """Fill a zmc_scan_desc.  For ZMC_MEM_DEVICE, ``values`` is a device
     pointer (int) or a torch CUDA float64 tensor."""
     keep = keep if keep is not None else _Keep()
@@ -484,6 +496,7 @@ def make_desc(gid, N, lo, hi, lengths, values=None, S=1, T=1, seed=0,
     d.stream = stream
     d.tile_lanes, d.tile_splits, d.tile_block = (int(x) for x in tiles)
     d.flags = int(flags)
+    d.chunk_points = int(chunk_points)
     return d, keep
 
 
@@ -497,11 +510,12 @@ def _ptr(x):
 
 def scan(gid, N, lo, hi, lengths, values, S, T, seed, precision=ZMC_FP32_KAHAN,
          first_index=0, count=-1, tiles=(0, 0, 0), flags=0, want_sums=False,
-         want_errw=True):
+         want_errw=True, chunk_points=0):
     """Host-memory scan through zmc_scan_ex; returns a dict of numpy arrays
     (mean, err, errw, [s1, s2]) and the zmc_scan_out."""
     d, keep = make_desc(gid, N, lo, hi, lengths, values, S, T, seed, precision,
-                        ZMC_MEM_HOST, first_index, count, None, tiles, flags)
+                        ZMC_MEM_HOST, first_index, count, None, tiles, flags,
+                        chunk_points=chunk_points)
     P = int(np.prod(np.asarray(lengths, np.int64)))
     n = (P - first_index) if count < 0 else count
     res = {"mean": np.empty(n), "err": np.empty(n)}
@@ -521,11 +535,12 @@ def scan(gid, N, lo, hi, lengths, values, S, T, seed, precision=ZMC_FP32_KAHAN,
 def scan_device(gid, N, lo, hi, lengths, values_dev, S, T, seed, out_mean, out_err,
                 out_errw=None, out_s1=None, out_s2=None, precision=ZMC_FP32_KAHAN,
                 first_index=0, count=-1, stream=None, workspace=None, tiles=(0, 0, 0),
-                flags=0):
+                flags=0, chunk_points=0):
     """Device-memory scan: values and outputs are torch CUDA float64 tensors;
     work is enqueued on ``stream`` (a cudaStream_t as int, or None)."""
     d, keep = make_desc(gid, N, lo, hi, lengths, values_dev, S, T, seed, precision,
-                        ZMC_MEM_DEVICE, first_index, count, stream, tiles, flags)
+                        ZMC_MEM_DEVICE, first_index, count, stream, tiles, flags,
+                        chunk_points=chunk_points)
     if workspace is not None:
         d.workspace = ctypes.c_void_p(workspace.data_ptr())
         d.workspace_bytes = workspace.numel() * workspace.element_size()

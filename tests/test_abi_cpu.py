@@ -91,6 +91,22 @@ def test_workspace_size_with_explicit_tiles_needs_no_gpu(lib):
     assert n >= 100 * 3 * 4 * 16
 
 
+def test_chunk_points_bound_the_workspace(lib):
+    """With explicit tiles the workspace holds one chunk of partial sums (and,
+    for host buffers, two chunks of outputs); chunk_points < 0 is refused."""
+    d, keep = _desc(lib, tiles=(32, 4, 256), mem=lib.ZMC_MEM_DEVICE, values=0x1000)
+    whole = lib.zmc_workspace_size(d)
+    assert whole == 100 * 3 * 4 * 16
+    d.chunk_points = 10
+    assert lib.zmc_workspace_size(d) == -(-10 * 3 * 4 * 16 // 256) * 256   # 256-byte aligned
+    d.chunk_points = -1
+    assert lib.zmc_validate(d) == lib.ZMC_EINVAL
+    h, keep2 = _desc(lib, tiles=(32, 4, 256))
+    one = lib.zmc_workspace_size(h)
+    h.chunk_points = 10
+    assert lib.zmc_workspace_size(h) < one
+
+
 def test_scan_without_gpu_fails_loudly(lib):
     import torch
     if torch.cuda.is_available():

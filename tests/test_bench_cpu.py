@@ -49,3 +49,50 @@ def test_sustainability_criterion():
     assert bench.sustainable(ok)
     assert not bench.sustainable(dict(ok, utilisation=1.1))
     assert not bench.sustainable(dict(ok, drain_s=6.0))
+
+
+def test_pipe_model_of_the_headline_kernel():
+    """Gaussian N = 4 in FP32-Kahan: 16 wide multiplies per evaluation
+    (20 per Philox call, 0.8 calls) bind at 32 per clock per SM."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cyc = bench.pipe_model(2, 4, 2)
+    assert cyc["fma_heavy"] == 16 / 32 and cyc["alu"] == 20 / 64
+    assert cyc["issue"] == 59 / 128 and cyc["xu"] == 1 / 32
+    b = bench.binding_pipe(2, 4, 2, 152, 2070.0, 4.41e11)
+    assert b["pipe"] == "fma_heavy"
+    assert abs(b["evals_per_s_at_full_pipe"] - 152 * 2070e6 * 2) < 1
+    assert 0.69 < b["frac"] < 0.71
+    # cos-product N = 8: still the wide multiplies (1.0) before the XU (0.5)
+    assert bench.binding_pipe(1, 8, 2, 152, 2070.0, 2e11)["pipe"] == "fma_heavy"
+    assert bench.pipe_model(0, 3, 2) == {}
+
+
+def test_ncu_table_round_trip(tmp_path):
+    """The ncu summariser maps launch names to (integrand, N, precision),
+    reads per-metric CSV rows and gives its markdown rows back."""
+    sys.path.insert(0, ROOT)
+    from paper_1910_01965_gb300 import ncu_table, workloads
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream",'
+           '"Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit",'
+           '"Metric Value"')
+    name = "void zmc::scan_kernel<4, zmc::Gauss32<4>, 2>(zmc::ScanArgs)"
+    rows = [hdr]
+    vals = {"sm__pipe_fmaheavy_cycles_active.sum": 2e9, "sm__cycles_elapsed.sum": 1e9,
+            "launch__registers_per_thread": 72, "smsp__inst_executed.sum": 1.5e9}
+    for m, v in vals.items():
+        rows.append('"0","1","python","h","%s","1","7","(256, 1, 1)","(9, 1, 1)","0","10.3",'
+                    '"Command line profiler metrics","%s","x","%s"' % (name, m, v))
+    rows.append('"1","1","python","h","void zmc::finalize_kernel(zmc::FinalizeArgs)","1","7",'
+                '"(256, 1, 1)","(9, 1, 1)","0","10.3","s","launch__registers_per_thread","x","30"')
+    out = ncu_table.summarise("==PROF== x\n" + "\n".join(rows))
+    assert len(out) == 1 and (out[0]["gid"], out[0]["N"], out[0]["prec"]) == (2, 4, 2)
+    ev = workloads.registry_scan(2, 4, **ncu_table.SMALL).evals
+    assert abs(out[0]["heavy_smsp_cycles_per_eval"] - 2e9 / ev) < 1e-12
+    assert abs(out[0]["heavy_busy_pct"] - 50.0) < 1e-9
+    assert out[0]["fp64_sm_cycles_per_eval"] != out[0]["fp64_sm_cycles_per_eval"]  # absent: nan
+    md = tmp_path / "s.md"
+    md.write_text(ncu_table.markdown(out, "cmd", "stamp123"))
+    stamp, table = ncu_table.read_summary(str(md))
+    assert stamp == "stamp123" and table[(2, 4, 2)]["registers"] == 72
+    assert ncu_table.kernel_key("scan_kernel<8, zmc::CosProd64<8>, 0>") == (1, 8, 0)

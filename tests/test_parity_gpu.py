@@ -282,11 +282,13 @@ def test_gauss_1e6_full_size_sampled(zmc, prec):
     assert np.all(np.isfinite(got["mean"])) and np.all(got["err"] > 0)
 
 
-@pytest.mark.parametrize("prec", [2, 1])
+@pytest.mark.parametrize("prec", [2, 1, 0])
 def test_osc_1e4_full_size_sampled(zmc, prec):
+    """The precision-stress workload at full size (10^4 points x 8 trials x
+    2^20 samples) in FP32-Kahan, plain FP32 and FP64, on sampled points."""
     spec = wl.scan_osc_1e4()
     got = _full_device(zmc, spec, prec)
-    pts = wl.sample_points(spec.P, 24)
+    pts = wl.sample_points(spec.P, 24 if prec else 16)
     ref = _oracle(spec, pts)
     sub = {k: v[pts] for k, v in got.items()}
     parity.check(sub, ref, _V(spec), spec.samples, prec, spec.name)

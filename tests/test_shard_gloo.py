@@ -77,3 +77,58 @@ def test_two_ranks_gloo_shard_gather_and_timing():
                                   spec.values, spec.samples, spec.trials, spec.seed)
     assert np.array_equal(full, whole["mean"])
     assert slowest == 2.0
+
+
+def _worker_sharded(rank, world, port, q):
+    """The benchmark's sharded pass (shard.sharded_scan): slices, barriers,
+    slowest-rank time, gather of per-point values and per-trial rows."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import time
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import oracle
+        from paper_1910_01965_gb300 import workloads as wl
+        spec = wl.scan_gauss_1e6(samples=1 << 8, trials=2)
+        spec.lists[0] = spec.lists[0][:3]          # 3 x 100 x 100 x 1 = 30,000 points
+        spec.lists[1] = spec.lists[1][:7]          # ... cut to 2,100 points
+
+        def scan_slice(first, count):
+            if rank == 1:
+                time.sleep(0.3)                    # the slower rank sets the time
+            pts = np.arange(first, first + count, dtype=np.int64)
+            res = oracle.default().scan_points(spec.integrand_id, spec.N, spec.lo, spec.hi,
+                                               spec.lengths, spec.values, spec.samples,
+                                               spec.trials, spec.seed, pts, nthreads=1,
+                                               want_sums=True)
+            return {"mean": res["mean"], "s1": res["s1"]}
+        full, slowest = shard.sharded_scan(spec.P, scan_slice)
+        if rank == 0:
+            q.put((full["mean"], full["s1"], slowest, spec.P))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_gloo_sharded_scan_helper():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_sharded, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    mean, s1, slowest, P = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    from oracle import oracle
+    from paper_1910_01965_gb300 import workloads as wl
+    spec = wl.scan_gauss_1e6(samples=1 << 8, trials=2)
+    spec.lists[0] = spec.lists[0][:3]
+    spec.lists[1] = spec.lists[1][:7]
+    whole = oracle.default().scan(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                                  spec.values, spec.samples, spec.trials, spec.seed,
+                                  want_sums=True)
+    assert P == spec.P and mean.shape == (P,) and s1.shape == (P, 2)
+    assert np.array_equal(mean, whole["mean"]) and np.array_equal(s1, whole["s1"])
+    assert slowest >= 0.3
