@@ -1,5 +1,9 @@
 """Build libzmc.so (the C-ABI CUDA library) in-tree with nvcc for sm_103a.
 
+    python -m paper_1910_01965_gb300.build            # libzmc.so
+    python -m paper_1910_01965_gb300.build --debug    # libzmc_debug.so (bounds checks)
+    python -m paper_1910_01965_gb300.build --variant NAME -DKNOB=V ...   # tuning variant
+
 Each sampling-kernel row (one precision x one integrand, N = 1..8) is its own
 translation unit of zmc_scan_inst.cu, so the objects compile in parallel.
 Objects go to paper_1910_01965_gb300/_build/, the library to
@@ -135,8 +139,18 @@ def build_debug(force: bool = False) -> str:
                  build_dir=BUILD_DEBUG)
 
 
+def build_variant(name: str, flags) -> str:
+    """A library built with extra compile-time knobs (e.g. -DZMC_CALLS_IN_FLIGHT=8),
+    as _build_<name>/libzmc.so; load it with ZMC_LIBRARY=<that path>."""
+    d = os.path.join(PKG, "_build_" + name)
+    return build(extra_flags=tuple(flags), lib=os.path.join(d, "libzmc.so"), build_dir=d)
+
+
 if __name__ == "__main__":
     if "--debug" in sys.argv:
         print(build_debug(force="--force" in sys.argv))
+    elif "--variant" in sys.argv:
+        i = sys.argv.index("--variant")
+        print(build_variant(sys.argv[i + 1], [a for a in sys.argv[i + 2:] if a.startswith("-D")]))
     else:
         print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

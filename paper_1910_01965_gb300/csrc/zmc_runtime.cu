@@ -223,8 +223,12 @@ int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out) {
 
 // --------------------------------------------------------------- planner --
 // Lanes per unit-split: the largest power of two <= 32 that still leaves each
-// lane >= 64 sample groups.  Splits: enough to give ~16 waves of resident
-// threads, never fewer than 64 groups per lane.  Block: 256 threads.
+// lane >= ZMC_PLAN_LANE_GROUPS sample groups.  Splits: enough to give ~16
+// waves of resident threads, never fewer than 64 groups per lane.  Block: 256
+// threads.
+#ifndef ZMC_PLAN_LANE_GROUPS
+#define ZMC_PLAN_LANE_GROUPS 64
+#endif
 TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count,
                     int threads_per_sm, int lanes_req, int splits_req, int block_req) {
   TilePlan tp;
@@ -234,7 +238,7 @@ TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count,
   int lanes = lanes_req;
   if (!lanes) {
     lanes = 32;
-    while (lanes > 1 && Q / lanes < 64) lanes >>= 1;
+    while (lanes > 1 && Q / lanes < ZMC_PLAN_LANE_GROUPS) lanes >>= 1;
     lanes = std::min(lanes, tp.block);
   }
   tp.lanes = lanes;
