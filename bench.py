@@ -670,8 +670,8 @@ def run_registry(args):
     kernel with its evaluations/s, its roofline on the SM issue peak from the
     algorithmic operations, the binding pipe of the algorithmic per-pipe model,
     and the committed ncu pipe figures of that kernel where they are current.
-    ``--registry-scale small`` runs each kernel once on a small grid (the ncu
-    capture of the registry profile)."""
+    ``--registry-scale small`` runs each kernel once on a 10^4-point grid with the
+    full-size scan's samples and tiles (the ncu capture of the registry profile)."""
     import torch
     from paper_1910_01965_gb300 import workloads as wl
     from paper_1910_01965_gb300 import zmc
@@ -690,22 +690,32 @@ def run_registry(args):
     summary = []
     for gid in gids:
         for N in Ns:
+            spec = wl.registry_scan(gid, N)
+            full_spec = spec
             if small:
-                spec = wl.registry_scan(gid, N, points=10_000, samples=1 << 13)
-            else:
-                spec = wl.registry_scan(gid, N)
+                spec = wl.registry_scan(gid, N, points=10_000)
             vals = torch.tensor(spec.values, dtype=torch.float64, device="cuda")
             mean = torch.empty(spec.P, dtype=torch.float64, device="cuda")
             err = torch.empty_like(mean)
             for pname in precs:
                 p = zmc.PRECISIONS[pname]
 
+                tiles = (0, 0, 0)
+                if small:
+                    # the full-size scan's tiles: each lane's work has the shape it
+                    # has in the timed sweep (same samples, lanes and splits)
+                    pf = zmc.scan(full_spec.integrand_id, N, full_spec.lo, full_spec.hi,
+                                  full_spec.lengths, full_spec.values, full_spec.samples,
+                                  full_spec.trials, full_spec.seed, precision=p,
+                                  flags=zmc.ZMC_F_PLAN_ONLY)[1]
+                    tiles = (pf.tile_lanes, pf.tile_splits, pf.tile_block)
+
                 def run(count=-1):
                     return zmc.scan_device(spec.integrand_id, spec.N, spec.lo, spec.hi,
                                            spec.lengths, vals, spec.samples, spec.trials,
                                            spec.seed, mean, err, precision=p,
                                            stream=stream.cuda_stream,
-                                           flags=zmc.ZMC_F_TIMINGS, count=count)
+                                           flags=zmc.ZMC_F_TIMINGS, count=count, tiles=tiles)
                 if small:
                     run()
                     continue
@@ -985,6 +995,8 @@ def main():
     ap.add_argument("--registry-n", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--registry-precisions", default="fp32_kahan,fp64")
     ap.add_argument("--registry-steps", type=int, default=3)
+    ap.add_argument("--tiles", default="",
+                    help="lanes,splits,block for the headline scan (default: the planner's)")
     ap.add_argument("--replicas", action="store_true",
                     help="with several GPUs: the whole grid per rank (own seed), weak scaling")
     args = ap.parse_args()
@@ -1054,10 +1066,19 @@ def main():
     # under its own seed instead (weak scaling).
     partition = world > 1 and not args.replicas
     first, count = shard.shard_range(spec.P, rank, world) if partition else (0, spec.P)
+    req = tuple(int(x) for x in args.tiles.split(",")) if args.tiles else (0, 0, 0)
+    if args.workload == "gauss_1e5" and not args.tiles:
+        # the profiling cut of the headline grid runs the headline's tiles, so its
+        # launch shape per unit is the 10^6-point scan's
+        full = bench_workload("gauss_1e6")
+        p6 = zmc.scan(full.integrand_id, full.N, full.lo, full.hi, full.lengths, full.values,
+                      full.samples, full.trials, full.seed, precision=prec,
+                      flags=zmc.ZMC_F_PLAN_ONLY)[1]
+        req = (p6.tile_lanes, p6.tile_splits, p6.tile_block)
     plan = zmc.scan(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
-                    spec.samples, spec.trials, spec.seed, precision=prec,
+                    spec.samples, spec.trials, spec.seed, precision=prec, tiles=req,
                     flags=zmc.ZMC_F_PLAN_ONLY)[1]
-    tiles = (plan.tile_lanes, plan.tile_splits, plan.tile_block) if partition else (0, 0, 0)
+    tiles = (plan.tile_lanes, plan.tile_splits, plan.tile_block) if partition else req
     rank_evals = count * spec.trials * spec.samples
 
     dev = torch.device("cuda", local)

@@ -45,6 +45,11 @@ constexpr int kBatchBlock = 256;
 // Sample groups per lane that bound one tile's work (tiles stay short next to
 // the whole batch, so the longest-first order balances the SMs).
 constexpr int64_t kBatchGroupsPerLane = 1024;
+// Lanes per unit-split: the largest power of two <= 32 leaving each lane at
+// least this many sample groups (plain FP32 lane sums: 64).
+#ifndef ZMC_BATCH_LANE_GROUPS
+#define ZMC_BATCH_LANE_GROUPS 64
+#endif
 
 TilePlan plan_batch_scan(const zmc_scan_desc* d) {
   TilePlan tp;
@@ -62,8 +67,9 @@ TilePlan plan_batch_scan(const zmc_scan_desc* d) {
   }
   int lanes = d->tile_lanes;
   if (!lanes) {
+    const int64_t min_groups = d->precision == ZMC_FP32 ? 64 : ZMC_BATCH_LANE_GROUPS;
     lanes = 32;
-    while (lanes > 1 && Q / lanes < 64) lanes >>= 1;
+    while (lanes > 1 && Q / lanes < min_groups) lanes >>= 1;
   }
   tp.lanes = std::min(lanes, kBatchBlock);
   int64_t splits = d->tile_splits;

@@ -16,9 +16,11 @@
 
 namespace zmc {
 
-__device__ __forceinline__ void finalize_point(const FinalizeArgs& a, int64_t i) {
+// Point i's statistics from its 2 T splits partial sums at `part` (global or
+// shared memory), summed in a fixed order.
+__device__ __forceinline__ void finalize_point_from(const FinalizeArgs& a, int64_t i,
+                                                    const double* part) {
   const double S = static_cast<double>(a.S);
-  const double* part = a.partial + 2 * (i * a.T) * a.splits;
   double sumI = 0.0, pooled = 0.0;
   for (int t = 0; t < a.T; ++t) {
     double s1 = 0.0, s2 = 0.0;
@@ -49,9 +51,30 @@ __device__ __forceinline__ void finalize_point(const FinalizeArgs& a, int64_t i)
     a.errw[i] = a.S > 1 ? a.V * sqrt(pooled / a.T / (static_cast<double>(a.T) * S)) : NAN;
 }
 
+__device__ __forceinline__ void finalize_point(const FinalizeArgs& a, int64_t i) {
+  finalize_point_from(a, i, a.partial + 2 * (i * a.T) * a.splits);
+}
+
+// The partial sums of a block's points are one contiguous range.  When it fits
+// in shared memory (2 T splits <= 24 at 256 threads) the block first copies it
+// with consecutive threads on consecutive doubles (coalesced reads), then each
+// thread sums its own point from shared memory; otherwise each thread reads its
+// point's sums from global memory.  The sums and their order are the same.
+constexpr int kFinalizeStageDoubles = 6144;  // 48 KB
+
 __global__ void finalize_kernel(const __grid_constant__ FinalizeArgs a) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < a.count) finalize_point(a, i);
+  __shared__ double stage[kFinalizeStageDoubles];
+  const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x;
+  const int64_t n = min(static_cast<int64_t>(blockDim.x), a.count - first);
+  const int64_t per = 2 * static_cast<int64_t>(a.T) * a.splits;
+  if (per * blockDim.x <= kFinalizeStageDoubles) {
+    const double* src = a.partial + first * per;
+    for (int64_t k = threadIdx.x; k < n * per; k += blockDim.x) stage[k] = src[k];
+    __syncthreads();
+    if (threadIdx.x < n) finalize_point_from(a, first + threadIdx.x, stage + threadIdx.x * per);
+  } else if (threadIdx.x < n) {
+    finalize_point(a, first + threadIdx.x);
+  }
 }
 
 // Every point of every scan of a batch: thread i finds its scan by binary

@@ -223,22 +223,28 @@ int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out) {
 
 // --------------------------------------------------------------- planner --
 // Lanes per unit-split: the largest power of two <= 32 that still leaves each
-// lane >= ZMC_PLAN_LANE_GROUPS sample groups.  Splits: enough to give ~16
-// waves of resident threads, never fewer than 64 groups per lane.  Block: 256
-// threads.
+// lane >= ZMC_PLAN_LANE_GROUPS sample groups (64 for plain FP32 lane sums,
+// whose rounding grows with their length).  Every lane ends with FP64 work
+// (its sums converted and reduced across the unit-split's lanes) on GB300's
+// narrow FP64 unit, so fewer, longer lanes are faster: measured on the
+// Gaussian 10^6-point scan (2^14 samples), 512 groups per lane (4 lanes)
+// +2.8 % over 64 (32 lanes).  Splits: enough to give ~16 waves of resident
+// threads, never fewer than 64 groups per lane.  Block: 256 threads.
 #ifndef ZMC_PLAN_LANE_GROUPS
-#define ZMC_PLAN_LANE_GROUPS 64
+#define ZMC_PLAN_LANE_GROUPS 512
 #endif
 TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count,
-                    int threads_per_sm, int lanes_req, int splits_req, int block_req) {
+                    int threads_per_sm, int lanes_req, int splits_req, int block_req,
+                    int precision) {
   TilePlan tp;
   const int G = group_samples(N);
   const int64_t Q = (S + G - 1) / G;
   tp.block = block_req ? block_req : 256;
   int lanes = lanes_req;
   if (!lanes) {
+    const int64_t min_groups = precision == ZMC_FP32 ? 64 : ZMC_PLAN_LANE_GROUPS;
     lanes = 32;
-    while (lanes > 1 && Q / lanes < ZMC_PLAN_LANE_GROUPS) lanes >>= 1;
+    while (lanes > 1 && Q / lanes < min_groups) lanes >>= 1;
     lanes = std::min(lanes, tp.block);
   }
   tp.lanes = lanes;
@@ -329,7 +335,7 @@ TilePlan plan_with(const zmc_scan_desc* d, int64_t count, int sm, int tps) {
     return tp;
   }
   return plan_tiles(d->N, d->samples_per_point, d->trials, count, sm, tps, d->tile_lanes,
-                    d->tile_splits, d->tile_block);
+                    d->tile_splits, d->tile_block, d->precision);
 }
 
 int plan_for(const zmc_scan_desc* d, int64_t count, TilePlan* tp) {

@@ -34,7 +34,7 @@ const char* last_error();
 
 int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out);
 TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count, int threads_per_sm,
-                    int lanes_req, int splits_req, int block_req);
+                    int lanes_req, int splits_req, int block_req, int precision);
 // The tile plan of a scan on a device with `sm` SMs of `tps` threads each:
 // an autotuner entry for the scan's class when the caller leaves the tiles
 // open and one is recorded (memory reads only), else plan_tiles.

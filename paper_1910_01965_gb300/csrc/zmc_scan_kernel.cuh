@@ -32,9 +32,8 @@ enum { kPrecFP64 = ZMC_FP64, kPrecFP32 = ZMC_FP32, kPrecFP32K = ZMC_FP32_KAHAN }
 #ifndef ZMC_LB_MIN_BLOCKS
 #define ZMC_LB_MIN_BLOCKS 1  // __launch_bounds__ minimum resident blocks
 #endif
-#ifndef ZMC_CALLS_IN_FLIGHT
-#define ZMC_CALLS_IN_FLIGHT 4  // independent Philox calls per lane per loop block
-#endif
+// ZMC_CALLS_IN_FLIGHT, when defined, overrides every functor's kCallsInFlight
+// (independent Philox calls per lane per loop block in the FP32 paths).
 
 template <int PREC>
 struct LaneAcc;
@@ -278,10 +277,14 @@ __device__ __forceinline__ void lane_groups(const uint32_t* __restrict__ rk0,
                                             LaneAcc<PREC>& acc) {
   constexpr int G = group_samples(N);
   constexpr int C = group_calls(N);
-  // Groups per loop block: about ZMC_CALLS_IN_FLIGHT independent Philox
-  // chains per lane (a group of C calls already has C).  The FP64 path is
-  // bound by its FP64 arithmetic, not by the stream: one group at a time.
+  // Groups per loop block: about kCallsInFlight independent Philox chains
+  // per lane (a group of C calls already has C).  The FP64 path is bound by
+  // its FP64 arithmetic, not by the stream: one group at a time.
+#ifdef ZMC_CALLS_IN_FLIGHT
   constexpr int kCalls = PREC == kPrecFP64 ? 1 : ZMC_CALLS_IN_FLIGHT;
+#else
+  constexpr int kCalls = PREC == kPrecFP64 ? 1 : F::kCallsInFlight;
+#endif
   constexpr int kBlock = kCalls / C > 1 ? kCalls / C : 1;
   // M0 * j for the lane's calls, carried along by 64-bit adds: call c of
   // group q has j = q C + c; the product for q C advances with the lane's

@@ -16,6 +16,7 @@ struct UserF32 {
   static constexpr bool kPerDim = false;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kCallsInFlight = 4;
   static constexpr int kFixedM = ZMC_M;
   using unit_t = float;
   float W[N], A[N], X[ZMC_M];
@@ -42,6 +43,7 @@ struct UserF64 {
   static constexpr bool kPerDim = false;
   static constexpr bool kTable = false;
   static constexpr bool kUsesSamples = true;
+  static constexpr int kCallsInFlight = 4;
   static constexpr int kFixedM = ZMC_M;
   using unit_t = double;
   double w[N], a[N], X[ZMC_M];

@@ -33,7 +33,7 @@ PIPES = [("heavy", "sm__pipe_fmaheavy_cycles_active.sum"),
          ("lite", "sm__pipe_fmalite_cycles_active.sum"),
          ("xu", "sm__pipe_xu_cycles_active.sum"),
          ("fp64", "sm__pipe_fp64_cycles_active.sum")]
-SMALL = {"points": 10_000, "samples": 1 << 13}   # the sweep's small grids
+SMALL = {"points": 10_000}   # the sweep's small grids (full-size samples and tiles)
 # Column suffix of each pipe's cycles per evaluation: SMSP-cycles (summed over
 # the four SMSPs of every SM) for the per-SMSP pipes, SM-cycles for FP64.
 UNIT = {"heavy": "_smsp_cycles_per_eval", "alu": "_smsp_cycles_per_eval",
@@ -120,7 +120,8 @@ GID_NAMES = {0: "const", 1: "cosprod", 2: "gauss03", 3: "poly", 4: "osc01", 5: "
 def markdown(rows: list, command: str, stamp: str) -> str:
     out = ["# Sampling kernels of the registry: ncu pipe figures per kernel", "",
            "Each row: one `scan_kernel<N, Functor, precision>` launch on the registry sweep's",
-           "small grid (about 10^4 points x 4 trials x 2^13 samples; `workloads.registry_scan`).",
+           "small grid (about 10^4 points x 4 trials x 2^15 samples, `workloads.registry_scan`,",
+           "with the tiles of the full-size sweep's 10^5-point scan).",
            "Cycles per evaluation on a pipe = that pipe's active cycles summed over the GPU /",
            "evaluations: SMSP-cycles for the FMA-heavy, ALU, FMA-lite and XU pipes (one per",
            "SMSP), SM-cycles for FP64 (one unit per SM on GB300).  A pipe busy every cycle would",
