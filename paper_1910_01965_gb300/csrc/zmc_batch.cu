@@ -46,9 +46,12 @@ constexpr int kBatchBlock = 256;
 // the whole batch, so the longest-first order balances the SMs).
 constexpr int64_t kBatchGroupsPerLane = 1024;
 // Lanes per unit-split: the largest power of two <= 32 leaving each lane at
-// least this many sample groups (plain FP32 lane sums: 64).
+// least this many sample groups (plain FP32 lane sums: 64).  Long lanes spend
+// less of their time in the FP64 epilogue on GB300's narrow FP64 unit:
+// measured, 512 against 64 makes the 2048 small scans of the serving mix 6 %
+// faster in one launch and leaves the uneven 256-scan batch unchanged.
 #ifndef ZMC_BATCH_LANE_GROUPS
-#define ZMC_BATCH_LANE_GROUPS 64
+#define ZMC_BATCH_LANE_GROUPS 512
 #endif
 
 TilePlan plan_batch_scan(const zmc_scan_desc* d) {

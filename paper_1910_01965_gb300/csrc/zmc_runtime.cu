@@ -224,12 +224,14 @@ int validate(const zmc_scan_desc* d, int64_t* P_out, int64_t* count_out) {
 // --------------------------------------------------------------- planner --
 // Lanes per unit-split: the largest power of two <= 32 that still leaves each
 // lane >= ZMC_PLAN_LANE_GROUPS sample groups (64 for plain FP32 lane sums,
-// whose rounding grows with their length).  Every lane ends with FP64 work
-// (its sums converted and reduced across the unit-split's lanes) on GB300's
-// narrow FP64 unit, so fewer, longer lanes are faster: measured on the
-// Gaussian 10^6-point scan (2^14 samples), 512 groups per lane (4 lanes)
-// +2.8 % over 64 (32 lanes).  Splits: enough to give ~16 waves of resident
-// threads, never fewer than 64 groups per lane.  Block: 256 threads.
+// whose rounding grows with their length), then doubled while the launch has
+// fewer than ~16 waves of resident threads and each lane keeps >= 64 groups.
+// Every lane ends with FP64 work (its sums converted and reduced across the
+// unit-split's lanes) on GB300's narrow FP64 unit, so fewer, longer lanes are
+// faster when the grid fills the GPU anyway: measured on the Gaussian
+// 10^6-point scan (2^14 samples), 4 lanes of 819 groups +2.8 % over 32 lanes
+// of 102.  Splits: enough to give ~16 waves of resident threads, never fewer
+// than 64 groups per lane.  Block: 256 threads.
 #ifndef ZMC_PLAN_LANE_GROUPS
 #define ZMC_PLAN_LANE_GROUPS 512
 #endif
@@ -241,18 +243,19 @@ TilePlan plan_tiles(int N, int64_t S, int T, int64_t count, int sm_count,
   const int64_t Q = (S + G - 1) / G;
   tp.block = block_req ? block_req : 256;
   int lanes = lanes_req;
+  const int64_t units = std::max<int64_t>(1, count * T);
+  const int64_t want = int64_t(16) * std::max(1, sm_count) * std::max(256, threads_per_sm);
   if (!lanes) {
     const int64_t min_groups = precision == ZMC_FP32 ? 64 : ZMC_PLAN_LANE_GROUPS;
     lanes = 32;
     while (lanes > 1 && Q / lanes < min_groups) lanes >>= 1;
+    while (lanes < 32 && units * lanes < want && Q / (2 * lanes) >= 64) lanes <<= 1;
     lanes = std::min(lanes, tp.block);
   }
   tp.lanes = lanes;
   int64_t splits = splits_req;
   if (!splits) {
-    const int64_t units = std::max<int64_t>(1, count * T);
     const int64_t base = units * lanes;
-    const int64_t want = int64_t(16) * std::max(1, sm_count) * std::max(256, threads_per_sm);
     splits = (want + base - 1) / base;
     const int64_t cap = std::max<int64_t>(1, Q / (int64_t(lanes) * 64));
     splits = std::max<int64_t>(1, std::min(splits, cap));
