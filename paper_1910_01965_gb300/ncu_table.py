@@ -159,15 +159,18 @@ def read_summary(path: str):
             "fp64_sm_cycles_per_eval", "heavy_busy_pct", "alu_busy_pct", "xu_busy_pct",
             "fp64_busy_pct"]
     key_re = re.compile(r"^g(\d+)_N(\d+)_p(\d+)$")
+    in_table = True          # the figures table comes first; later sections are prose
     for line in open(path):
         if line.startswith("kernel_source_stamp:"):
             stamp = line.split(":", 1)[1].strip()
             continue
-        if not line.startswith("| g"):
+        if line.startswith("## "):
+            in_table = False
+        if not in_table or not line.startswith("| g"):
             continue
         f = [x.strip() for x in line.strip().strip("|").split("|")]
         m = key_re.match(f[0])
-        if not m:
+        if not m or len(f) != len(cols) + 1:
             continue
         vals = {}
         for c, v in zip(cols, f[1:]):
