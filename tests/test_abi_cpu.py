@@ -128,3 +128,19 @@ def test_product_package_does_not_import_oracle():
         if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
             src = open(path, errors="replace").read()
             assert "oracle" not in src.lower() or path.endswith("workloads.py"), path
+
+
+def test_log_level_one_reports_failed_calls(lib):
+    """ZMC_LOG=1 writes each failed call's message to stderr (a child process,
+    no GPU needed: validation fails before any device work)."""
+    import subprocess
+    import sys
+    code = ("import numpy as np\n"
+            "from paper_1910_01965_gb300 import zmc\n"
+            "d, k = zmc.make_desc(1, 2, [0, 0], [1, 1], [10, 0], np.zeros(10), 8, 2, 0)\n"
+            "print(zmc.zmc_validate(d))\n")
+    for level, expect in (("1", True), ("0", False)):
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                           env=dict(os.environ, ZMC_LOG=level), timeout=120)
+        assert r.returncode == 0 and r.stdout.strip() == "1", r.stderr[-1000:]
+        assert ("[zmc:1]" in r.stderr and "list 1 has length 0" in r.stderr) == expect, r.stderr
