@@ -157,9 +157,11 @@ static int tune(const zmc_scan_desc* d0, int budget_ms, zmc_tune_result* out) {
   best.evals_per_s = dflt;
   best.default_evals_per_s = dflt;
   int tried = 1;
-  const int lanes_c[] = {4, 8, 16, 32, 64, 128};
+  // Candidates: the long lanes the planner favours (each lane's FP64 epilogue
+  // runs on the narrow FP64 unit) down to the wide ones of small grids.
+  const int lanes_c[] = {1, 2, 4, 8, 16, 32, 64, 128};
   const int block_c[] = {256, 128, 512};
-  const int gpl_c[] = {1024, 256, 4096};
+  const int gpl_c[] = {1024, 256, 4096, 8192};
   for (int gpl : gpl_c) {
     for (int block : block_c) {
       for (int lanes : lanes_c) {
