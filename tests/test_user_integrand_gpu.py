@@ -34,6 +34,13 @@ def test_user_cosprod_matches_the_oracle(z):
             got, o = z.scan(gid, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
                             spec.samples, spec.trials, spec.seed, precision=prec)
             parity.check(got, ref, V, spec.samples, prec, "user cosprod N=%d" % spec.N)
+            # the run-time-compiled kernel through a chunked scan: the same bits
+            chunked, oc = z.scan(gid, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
+                                 spec.samples, spec.trials, spec.seed, precision=prec,
+                                 chunk_points=7)
+            assert oc.chunks == -(-spec.P // 7) and oc.chunks > 1
+            for k in got:
+                assert np.array_equal(chunked[k], got[k]), (spec.N, prec, k)
 
 
 def test_new_integrand_against_its_closed_form(z):
