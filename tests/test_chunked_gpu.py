@@ -178,3 +178,32 @@ def test_more_than_2_31_blocks_in_one_call(zmc):
     got = {"mean": m.cpu().numpy()[pts], "err": e.cpu().numpy()[pts],
            "errw": w.cpu().numpy()[pts]}
     parity.check(got, ref, 1.0, spec.samples, 2, spec.name)
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_chunked_host_scan_with_only_mean_and_err_and_timings(zmc, pinned):
+    """The optional outputs left NULL, timings on, chunk_points beyond the
+    slice (one chunk) and a ragged last chunk: the same bits as one chunk,
+    and the exposed copy time is what is left after the last chunk."""
+    import torch
+    spec = _spec()
+
+    def run(cp):
+        if pinned:
+            m = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+            e = torch.empty(spec.P, dtype=torch.float64).pin_memory().numpy()
+        else:
+            m, e = np.empty(spec.P), np.empty(spec.P)
+        d, keep = zmc.make_desc(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths,
+                                spec.values, spec.samples, spec.trials, spec.seed, 2,
+                                flags=zmc.ZMC_F_TIMINGS, chunk_points=cp)
+        o = zmc.zmc_scan_out()
+        o.mean, o.err = zmc._ptr(m), zmc._ptr(e)
+        zmc.zmc_scan_ex(d, o)
+        return m, e, o
+    m1, e1, o1 = run(10 * spec.P)
+    assert o1.chunks == 1
+    m5, e5, o5 = run(2500)                  # 5 chunks, the last one ragged
+    assert o5.chunks == 5 and o5.launches == 10
+    assert np.array_equal(m1, m5) and np.array_equal(e1, e5)
+    assert o5.kernel_ms > 0 and o5.finalize_ms > 0 and 0 <= o5.d2h_ms <= o5.total_ms
