@@ -14,8 +14,10 @@
  * (shortest remaining work first, with a share of every step reserved for the
  * oldest request so large scans keep moving); partial sums stay on the device
  * between steps.  Grids too large for one chunk are streamed: each chunk of
- * grid points is finalized as soon as its tiles are done and copied to the
- * host on a separate stream while later steps compute.  The paper cuts grids
+ * grid points is finalized as soon as its tiles are done and copied into the
+ * caller's host arrays by a copier thread, on a separate stream, while later
+ * steps compute (the scheduler never waits for a copy, so pageable output
+ * arrays do not hold up the planning of the next step).  The paper cuts grids
  * into batches for its GPUs (Sec. 2); this is that cut, made dynamic on one
  * GPU.
  *
