@@ -292,3 +292,18 @@ def test_osc_1e4_full_size_sampled(zmc, prec):
     ref = _oracle(spec, pts)
     sub = {k: v[pts] for k, v in got.items()}
     parity.check(sub, ref, _V(spec), spec.samples, prec, spec.name)
+
+
+@pytest.mark.parametrize("prec", [2, 1, 0])
+def test_registry_scans_at_scale_sampled(zmc, prec):
+    """Every (integrand, N) of the registry at the sweep's scale (FP32-Kahan and
+    FP32: 10^5 points x 4 trials x 2^15 samples; FP64: 2 x 10^4 points) with
+    the planner's tiles, against the oracle on 4 seeded points per scan."""
+    for gid in (1, 2, 3, 4, 5):
+        for N in range(1, 9):
+            spec = wl.registry_scan(gid, N, points=10 ** 5 if prec else 2 * 10 ** 4)
+            got = _full_device(zmc, spec, prec)
+            pts = wl.sample_points(spec.P, 4, seed=100 * gid + N)
+            ref = _oracle(spec, pts)
+            sub = {k: v[pts] for k, v in got.items()}
+            parity.check(sub, ref, _V(spec), spec.samples, prec, spec.name)
