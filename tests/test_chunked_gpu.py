@@ -207,3 +207,17 @@ def test_chunked_host_scan_with_only_mean_and_err_and_timings(zmc, pinned):
     assert o5.chunks == 5 and o5.launches == 10
     assert np.array_equal(m1, m5) and np.array_equal(e1, e5)
     assert o5.kernel_ms > 0 and o5.finalize_ms > 0 and 0 <= o5.d2h_ms <= o5.total_ms
+
+
+def test_chunk_counts_of_empty_and_plan_only_calls(zmc):
+    """An empty slice runs no chunk; ZMC_F_PLAN_ONLY reports the chunks a call
+    would take without computing."""
+    spec = _spec()
+    res, o = zmc.scan(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
+                      spec.samples, spec.trials, spec.seed, first_index=spec.P, count=0,
+                      chunk_points=5)
+    assert o.chunks == 0 and o.launches == 0
+    res, o = zmc.scan(spec.integrand_id, spec.N, spec.lo, spec.hi, spec.lengths, spec.values,
+                      spec.samples, spec.trials, spec.seed, chunk_points=1000,
+                      flags=zmc.ZMC_F_PLAN_ONLY)
+    assert o.chunks == -(-spec.P // 1000) and o.launches == 0
