@@ -140,10 +140,12 @@ def build_debug(force: bool = False) -> str:
 
 
 def build_variant(name: str, flags) -> str:
-    """A library built with extra compile-time knobs (e.g. -DZMC_CALLS_IN_FLIGHT=8),
-    as _build_<name>/libzmc.so; load it with ZMC_LIBRARY=<that path>."""
-    d = os.path.join(PKG, "_build_" + name)
-    return build(extra_flags=tuple(flags), lib=os.path.join(d, "libzmc.so"), build_dir=d)
+    """A library built with extra compiler flags (e.g. -DZMC_CALLS_IN_FLIGHT=8), as
+    libzmc_<name>.so beside the default one (its objects in _build_<name>/), so that
+    it finds the kernel headers in csrc/ as the default library does; load it with
+    ZMC_LIBRARY=<that path>."""
+    return build(extra_flags=tuple(flags), lib=os.path.join(PKG, "libzmc_%s.so" % name),
+                 build_dir=os.path.join(PKG, "_build_" + name))
 
 
 if __name__ == "__main__":
@@ -151,6 +153,6 @@ if __name__ == "__main__":
         print(build_debug(force="--force" in sys.argv))
     elif "--variant" in sys.argv:
         i = sys.argv.index("--variant")
-        print(build_variant(sys.argv[i + 1], [a for a in sys.argv[i + 2:] if a.startswith("-D")]))
+        print(build_variant(sys.argv[i + 1], [a for a in sys.argv[i + 2:] if a.startswith("-")]))
     else:
         print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
